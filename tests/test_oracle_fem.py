@@ -1,0 +1,153 @@
+"""Pins for the fine-mesh oracle (O-FEM) against closed forms and invariants.
+
+Each test checks the oracle against something other than itself: the algebra of
+a rigid motion, the exactness of Q1 elements for linear fields (patch test),
+free thermal expansion, and the Lame solution for a Cu cylinder in Si.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+
+def rigid_modes(coords):
+    """Six rigid-body motions evaluated at the given node coordinates, (3N, 6)."""
+    n = coords.shape[0]
+    R = np.zeros((3 * n, 6))
+    for c in range(3):
+        R[c::3, c] = 1.0
+    x, y, z = coords.T
+    # rotations about x, y, z: omega x r
+    R[1::3, 3], R[2::3, 3] = -z, y
+    R[0::3, 4], R[2::3, 4] = z, -x
+    R[0::3, 5], R[1::3, 5] = -y, x
+    return R
+
+
+def test_von_mises_special_cases():
+    s = 123.0
+    assert fem.von_mises(np.array([s, 0, 0, 0, 0, 0])) == pytest.approx(s)          # uniaxial
+    assert fem.von_mises(np.array([0, 0, 0, s, 0, 0])) == pytest.approx(np.sqrt(3) * s)  # pure shear
+    assert fem.von_mises(np.array([s, s, s, 0, 0, 0])) == pytest.approx(0.0, abs=1e-12)  # hydrostatic
+    # biaxial equal tension: sigma_vm = s
+    assert fem.von_mises(np.array([s, s, 0, 0, 0, 0])) == pytest.approx(s)
+
+
+def test_lame_parameters_closed_form():
+    # E = 2 mu (1 + nu) and the bulk modulus K = lam + 2 mu / 3 = E / (3 (1 - 2 nu))
+    for mat in fem.DEFAULT_MATERIALS:
+        lam, mu = fem.lame(mat)
+        assert 2 * mu * (1 + mat.nu) == pytest.approx(mat.E, rel=1e-14)
+        assert lam + 2 * mu / 3 == pytest.approx(mat.E / (3 * (1 - 2 * mat.nu)), rel=1e-14)
+
+
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.8, 0.5, 2.5)])
+def test_element_stiffness_invariants(h):
+    Ke, fe = fem.element_matrices(h, fem.CU)
+    assert np.abs(Ke - Ke.T).max() <= 1e-12 * np.abs(Ke).max()
+    w = np.linalg.eigvalsh(Ke)
+    assert w[:6].max() <= 1e-10 * w[-1]          # exactly six zero modes
+    assert w[6] > 1e-3 * w[-1]                    # and no spurious seventh
+    corners = np.array([[(l & 1) * h[0], ((l >> 1) & 1) * h[1], ((l >> 2) & 1) * h[2]] for l in range(8)])
+    R = rigid_modes(corners)
+    assert np.abs(Ke @ R).max() <= 1e-10 * np.abs(Ke).max()
+    # a uniform dT on a free element is self-equilibrated: the load does no work on rigid motions
+    assert np.abs(R.T @ fe).max() <= 1e-9 * np.abs(fe).max()
+
+
+def _linear_field(coords, G, t):
+    return (coords @ G.T + t).ravel()
+
+
+@pytest.mark.parametrize("dT", [0.0, -250.0])
+def test_patch_test_linear_field_is_exact(dT):
+    """Prescribing a linear displacement on the boundary of a homogeneous
+    block must reproduce it exactly inside, with constant stress D eps - tm dT 1."""
+    mesh = fem.BoxMesh(3.0, 2.0, 4.0, 3, 4, 3, np.zeros(36, dtype=np.int64))
+    A, b = fem.assemble(mesh)
+    coords = mesh.node_coords()
+    G = np.array([[1e-3, 2e-3, -1e-3], [0.5e-3, -2e-3, 1e-3], [3e-3, 0.0, 1e-3]])
+    t = np.array([0.1, -0.2, 0.3])
+    u_exact = _linear_field(coords, G, t)
+    bnd = np.flatnonzero(mesh.boundary_node_mask())
+    fixed = (3 * bnd[:, None] + np.arange(3)).ravel()
+    u = fem.solve_dirichlet(A, dT * b, fixed, u_exact[fixed])
+    assert np.abs(u - u_exact).max() <= 1e-12 * np.abs(u_exact).max()
+    sig = fem.gauss_stresses(mesh, u, dT)
+    eps = np.array([G[0, 0], G[1, 1], G[2, 2], G[0, 1] + G[1, 0], G[1, 2] + G[2, 1], G[2, 0] + G[0, 2]])
+    expect = fem.elasticity_matrix(fem.SI) @ eps - fem.thermal_modulus(fem.SI) * dT * fem.VOIGT_ONE
+    assert np.abs(sig - expect).max() <= 1e-9 * np.abs(expect).max()
+
+
+def test_free_thermal_expansion_is_stress_free():
+    """Homogeneous body, uniform dT, statically determinate (3-2-1) supports:
+    u = alpha dT (x - x0) exactly and sigma = 0 (thermal load of Eq. 5)."""
+    mesh = fem.BoxMesh(4.0, 3.0, 5.0, 4, 3, 5, np.zeros(60, dtype=np.int64))
+    A, b = fem.assemble(mesh)
+    nid = mesh.node_index()
+    n0, n1, n2 = nid[0, 0, 0], nid[-1, 0, 0], nid[0, -1, 0]
+    fixed = np.array([3 * n0, 3 * n0 + 1, 3 * n0 + 2, 3 * n1 + 1, 3 * n1 + 2, 3 * n2 + 2])
+    dT = -250.0
+    u = fem.solve_dirichlet(A, dT * b, fixed, np.zeros(6))
+    u_exact = (fem.SI.alpha * dT * mesh.node_coords()).ravel()
+    assert np.abs(u - u_exact).max() <= 1e-10 * np.abs(u_exact).max()
+    sig = fem.gauss_stresses(mesh, u, dT)
+    assert np.abs(sig).max() <= 1e-8 * fem.thermal_modulus(fem.SI) * abs(dT)
+
+
+def lame_cylinder(a, cu, si, dT):
+    """Closed-form plane-strain thermal misfit of a cylinder (radius a, material
+    cu) in an infinite matrix (si) whose far field expands freely in plane.
+    u_r = A1 r inside, u_r = A2 r + B/r outside with A2 = (1 + nu_si) alpha_si dT."""
+    lam1, mu1 = fem.lame(cu)
+    lam2, mu2 = fem.lame(si)
+    k1 = lam1 + mu1
+    A2 = (1 + si.nu) * si.alpha * dT
+    B = a * a * k1 * ((1 + cu.nu) * cu.alpha - (1 + si.nu) * si.alpha) * dT / (k1 + mu2)
+    return A2, B, mu2
+
+
+def _lame_case(N):
+    a = 2.5
+    Lh = 8.0 * a
+    dT = -250.0
+    mesh = fem.BoxMesh(2 * Lh, 2 * Lh, 1.0, N, N, 1, np.zeros(N * N, dtype=np.int64))
+    c = mesh.element_centroids() - np.array([Lh, Lh, 0.0])
+    mesh.mat_id = np.where(np.hypot(c[:, 0], c[:, 1]) <= a, 1, 0)
+    A, b = fem.assemble(mesh)
+    A2, B, mu2 = lame_cylinder(a, fem.CU, fem.SI, dT)
+    X = mesh.node_coords() - np.array([Lh, Lh, 0.0])
+    r = np.maximum(np.hypot(X[:, 0], X[:, 1]), 1e-30)   # only boundary nodes (r >= 8a) are used
+    ur = A2 * r + B / r
+    u_ex = np.zeros_like(X)
+    u_ex[:, 0] = ur * X[:, 0] / r
+    u_ex[:, 1] = ur * X[:, 1] / r
+    u_ex = u_ex.ravel()
+    nodes = np.arange(mesh.n_nodes)
+    lateral = np.flatnonzero((np.abs(X[:, 0]) > Lh - 1e-9) | (np.abs(X[:, 1]) > Lh - 1e-9))
+    fixed = np.concatenate([3 * nodes + 2, 3 * lateral, 3 * lateral + 1])   # plane strain u_z = 0
+    u = fem.solve_dirichlet(A, dT * b, fixed, u_ex[fixed])
+    sig = fem.gauss_stresses(mesh, u, dT).mean(axis=1)
+    rc = np.hypot(c[:, 0], c[:, 1])
+    sel = (rc >= 1.5 * a) & (rc <= 3.0 * a)
+    ct, st = c[sel, 0] / rc[sel], c[sel, 1] / rc[sel]
+    s = sig[sel]
+    srr = s[:, 0] * ct ** 2 + s[:, 1] * st ** 2 + 2 * s[:, 3] * ct * st
+    stt = s[:, 0] * st ** 2 + s[:, 1] * ct ** 2 - 2 * s[:, 3] * ct * st
+    ref = 2 * mu2 * B / a ** 2                       # |sigma| at the interface
+    err = max(np.abs(srr + 2 * mu2 * B / rc[sel] ** 2).max(), np.abs(stt - 2 * mu2 * B / rc[sel] ** 2).max()) / abs(ref)
+    szz_err = np.abs(s[:, 2] + fem.SI.E * fem.SI.alpha * dT).max() / abs(fem.SI.E * fem.SI.alpha * dT)
+    return err, szz_err
+
+
+def test_lame_cylinder_closed_form():
+    """Eq. 1 physics against the Lame plane-strain solution: the error near the
+    via (r in [1.5a, 3a]) falls under refinement and ends within a few percent
+    (the voxel staircase makes it first order)."""
+    errs = [_lame_case(N) for N in (40, 80, 160)]
+    e = [x[0] for x in errs]
+    assert e[0] > e[1] > e[2]
+    assert e[2] < 0.05
+    assert errs[2][1] < 0.02      # sigma_zz = -E alpha dT in the matrix (plane strain)
