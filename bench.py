@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark of the MORE-Stress global stage on one GB300.
+
+Workload: the 100x100 TSV array of 10x10x50 um blocks (Cu TSV radius 2.5 um,
+0.5 um SiO2 liner, 12x12x10 Q1 hex mesh, degree-2 face basis, m = 78), every
+site occupied, dT = -250 K, bottom clamped. One step = one global-stage solve
+(mstress_solve) plus the per-element von Mises recovery of every block
+(mstress_recover, VM_ELEM) through the C ABI; the reduced block models are
+built once beforehand on the GPU (the one-shot local stage, not timed).
+
+Metric: TSV blocks solved+recovered per second. With --gpus N (torchrun) every
+rank runs its own replica of the workload (weak scaling, no collective on the
+data path); the value is all ranks' blocks over the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (plain FP64 reduced model with a
+sparse direct solve) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TSV blocks solved+recovered/s (100x100 array)"
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+DTYPE = {"fp64": "f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64", "bf16x3": "bf16x3+f32+f64"}
+ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--nx", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ CPU oracle
+ORACLE_CODE = r"""
+import json, sys, time, os
+sys.path.insert(0, {root!r})
+import numpy as np, warnings
+warnings.simplefilter("ignore")
+from oracle import fem, mor
+from paper_2411_12690_gb300 import workloads as W
+spec = W.BLOCK_SMALL
+mesh = fem.tsv_block_mesh(spec.lx, spec.ly, spec.lz, spec.ex, spec.ey, spec.ez, spec.r_cu, spec.t_liner)
+blk = mor.local_stage(mesh, (3, 3, 3))                 # local stage: not part of the timed sample
+st = W.site_types({side}, {side}, 1.0)
+times = []
+for k in range({reps}):
+    t0 = time.perf_counter()
+    sol = mor.global_stage([blk], st, W.DT_DEFAULT)
+    vm = mor.recover_vm([blk], sol)
+    times.append(time.perf_counter() - t0)
+print(json.dumps(dict(times=times, blocks=int(st.size))))
+"""
+
+
+def run_oracle(side: int, reps: int) -> dict:
+    """Time the oracle's online part (assembly + direct solve + recovery) in a
+    fresh single-threaded interpreter."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_CODE.format(root=ROOT, side=side, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(res: dict) -> dict:
+    t = statistics.median(res["times"])
+    return {"value": res["blocks"] / t, "unit": "blocks/s", "cores": 1, "kind": "oracle",
+            "sample": f"{ORACLE_SIDE}x{ORACLE_SIDE} array of the same block (assembly + sparse direct solve + "
+                      f"von Mises recovery of every block, FP64), median of {len(res['times'])} runs; the "
+                      f"direct solve grows faster than linearly, so this overstates the oracle at 100x100"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle(ORACLE_SIDE, args.warmup + args.steps)
+    times = res["times"][args.warmup:]
+    blocks = res["blocks"]
+    total = sum(times)
+    value = blocks * len(times) / total
+    cb = cpu_baseline_entry(dict(times=times, blocks=blocks))
+    cb["value"] = value
+    line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"oracle sample: {ORACLE_SIDE}x{ORACLE_SIDE} array of the 10x10x50 um TSV block "
+                                   f"(12x12x10 hex mesh, degree-2 basis, m=78), dT=-250 K, bottom clamped",
+                       "sample_of": "100x100 array", "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ GPU arm
+def ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_res = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_res = run_oracle(ORACLE_SIDE, 3)      # before any GPU work in this process
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2411_12690_gb300 import _lib as L
+    from paper_2411_12690_gb300 import api
+    from paper_2411_12690_gb300 import workloads as W
+
+    prec = PREC[args.precision]
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(stream=stream.cuda_stream, precision=prec)
+    spec = W.BLOCK_SMALL
+    blks = [ctx.build_block(spec), ctx.build_block(spec.dummy())]
+    n_el = spec.ex * spec.ey * spec.ez
+    nx = ny = args.nx
+    st = W.site_types(nx, ny, 1.0)
+    n_blocks = nx * ny
+    vm_dtype = torch.float64 if prec == 0 else torch.float32
+    vm_dev = torch.empty(n_blocks * n_el, dtype=vm_dtype, device="cuda")
+    vm_host = torch.empty(n_blocks * n_el, dtype=vm_dtype).pin_memory()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")    # > 129 MB L2
+
+    def step(out):
+        sol = ctx.solve(st, blks, W.DT_DEFAULT)
+        sol.recover(L.MSTRESS_VM_ELEM, out=out)
+        return sol
+
+    for _ in range(args.warmup):
+        step(vm_dev).close()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = api.launch_count()
+    total_ms = 0.0
+    infos = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sol = step(vm_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        infos.append(sol.info())
+        sol.close()
+    launches = api.launch_count() - l0
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * n_blocks * args.steps / (total_ms / 1e3)
+
+    # end to end: host inputs (site map, dT) in, von Mises to pinned host memory, every step
+    e2e_t = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = ctx.solve(st, blks, W.DT_DEFAULT)
+        s2.recover(L.MSTRESS_VM_ELEM, out=vm_host)
+        e2e_t += time.perf_counter() - t0
+        s2.close()
+    et = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_value = world * n_blocks * args.steps / float(et.item())
+
+    # roofline of the dominant kernel, timed live with CUDA events on the context stream
+    sol = step(vm_dev)
+    info = sol.info()
+    t_apply = api.profile(ctx, sol, 0, 20)
+    t_isum = api.profile(ctx, sol, 1, 20)
+    t_rec = api.profile(ctx, sol, 3, 5)
+    n_iter = info["iters"]
+    share = {"apply": t_apply * n_iter, "isum": t_isum * n_iter, "recover": t_rec}
+    m = 78
+    apply_flops = 2.0 * m * m * n_blocks * (3 if prec == 3 else 1)
+    rec_flops = 2.0 * 6 * n_el * (m + 1) * n_blocks * (3 if prec == 3 else 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_mhz = clk.get("sm_mhz") or 1900.0
+    if prec == 0:
+        # FP64 pipe: 152 SMs x 2 DFMA/clk (4 flop/clk) at the sampled SM clock
+        fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
+        dom = max(share, key=share.get) if share["recover"] > share["apply"] else "apply"
+        if dom == "recover":
+            roof = {"bound": "alu", "achieved": rec_flops / (t_rec * 1e-3) / 1e12, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "traffic": None, "kernel": "k_recover<FP64> (von Mises epilogue)"}
+        else:
+            roof = {"bound": "alu", "achieved": apply_flops / (t_apply * 1e-3) / 1e12, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "traffic": None, "kernel": "k_apply64 (element products, FP64)"}
+        roof["peak_source"] = "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock"
+    else:
+        roof = {"bound": "alu", "achieved": apply_flops / (t_apply * 1e-3) / 1e12,
+                "peak": 152 * 256 * sm_mhz * 1e6 / 1e12, "unit": "TFLOP/s", "traffic": None,
+                "kernel": "k_apply32 (element products, reduced precision on CUDA cores)",
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x sampled SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["avg_launch_ms"] = {"apply": t_apply, "isum": t_isum, "recover": t_rec}
+    sol.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+                "config": {"workload": f"{nx}x{ny} TSV array, 10x10x50 um blocks, Cu r=2.5 um + 0.5 um SiO2 liner, "
+                                       f"12x12x10 Q1 hex mesh, degree-2 face basis (m=78), all sites occupied, "
+                                       f"dT=-250 K, bottom clamped; solve + per-element von Mises",
+                           "precision": args.precision, "blocks": n_blocks, "pcg_iters": info["iters"],
+                           "refinement_steps": info["outer"], "rel_res": info["rel_res"],
+                           "l2": "flushed before every timed step (512 MB write)",
+                           "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+                "roofline": roof,
+                "e2e": {"value": e2e_value, "unit": "blocks/s", "h2d_bytes_per_step": int(st.size + 8),
+                        "d2h_bytes_per_step": int(vm_host.numel() * vm_host.element_size())},
+                "gpu_launches": int(launches),
+                "clocks": clk}
+        if cpu_res is not None:
+            line["cpu_baseline"] = cpu_baseline_entry(cpu_res)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

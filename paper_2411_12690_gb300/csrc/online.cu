@@ -1,0 +1,1222 @@
+// Global stage of MORE-Stress (section 4.3, Eq. 20) on the GPU.
+//
+// The reduced global system A_global u = b_global is never assembled. Blocks
+// act as abstract elements (section 4.3): block (i, j) of an nx*ny array owns
+// the Lagrange-lattice points (i(n-1)+a, j(n-1)+b, c) of its surface nodes
+// (a, b, c), so the element-to-global map is arithmetic. One PCG iteration is
+//   1. apply:   Y_e = A_element[type e] * p[G_e]   for every block e   (Eq. 18)
+//   2. isum:    q_g = sum of Y_e over the <= 4 blocks owning lattice DOF g,
+//               in a fixed order (bitwise reproducible), and <p, q> partials
+//   3. vec1:    alpha, x += alpha p, r -= alpha q, z = D^-1 r, <r,z>, <r,r> partials
+//   4. vec2:    beta, p = z + beta p
+//   5. scalars: per-array reductions, stopping test, iteration count
+// Every phase is one launch over the work items of all arrays of a batch
+// (a grid-stride "persistent" loop), each array with its own scalars. The
+// iteration is captured once as a CUDA graph and replayed. Constrained DOFs
+// (clamped faces, prescribed values) have D^-1 = 0, which keeps r, z, p zero
+// there; prescribed values enter b by lifting (Eq. 13).
+//
+// Precision: FP64 vectors and FP64 operator in the plain mode; in the mixed
+// modes an FP64 outer loop (residual b - A x with the FP64 operator) drives an
+// inner PCG with FP32 vectors and a reduced-precision operator, while all dot
+// products and step lengths stay FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <type_traits>
+
+#include "solve.h"
+
+namespace ms {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ----------------------------------------------------------- reductions
+// Fixed-order sum of n values by one warp: lane-strided partial sums, then a
+// butterfly. Every caller that folds the same array gets the same bits.
+__device__ __forceinline__ double warp_fold(const double* v, int n) {
+    const int lane = threadIdx.x & 31;
+    double s = 0;
+    for (int i = lane; i < n; i += 32) s += v[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Block sum (kThreads threads) in a fixed order; result valid in all threads.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    return t;
+}
+
+__device__ __forceinline__ void lattice_coords(const ArrayDev& A, long long g, int& comp, int& gx, int& gy,
+                                               int& gz) {
+    long long l = g - A.vec_off;
+    long long node = l / 3;
+    comp = (int)(l - 3 * node);
+    gx = (int)(node % A.X);
+    long long t = node / A.X;
+    gy = (int)(t % A.Y);
+    gz = (int)(t / A.Y);
+}
+
+// Visit the blocks that own lattice point (gx, gy, gz) with the point's
+// surface-node index there, rows ascending then columns ascending.
+template <class Fn>
+__device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __restrict__ surf, int n, int gx,
+                                           int gy, int gz, Fn fn) {
+    const int n1 = n - 1;
+    int ih = gx / n1, il = (gx % n1 == 0) ? ih - 1 : ih;
+    int jh = gy / n1, jl = (gy % n1 == 0) ? jh - 1 : jh;
+    ih = min(ih, A.nx - 1);
+    jh = min(jh, A.ny - 1);
+    il = max(il, 0);
+    jl = max(jl, 0);
+    for (int j = jl; j <= jh; ++j)
+        for (int i = il; i <= ih; ++i) {
+            int a = gx - i * n1, b = gy - j * n1;
+            int s = __ldg(surf + (gz * n + b) * n + a);
+            if (s >= 0) fn(A.block_off + (long long)j * A.nx + i, s);
+        }
+}
+
+// ---------------------------------------------------------- a2: rhs, diag
+struct RhsArgs {
+    const VecWork* vwork;
+    int n_vwork;
+    const ArrayDev* arrays;
+    const LocalMap* lm;
+    const uint8_t* site;
+    const uint8_t* fixed;   // optional per-DOF prescribed marker
+    TypeTab tt;
+    int m;
+    double* b;
+    double* dinv;
+};
+
+// b = dT sum_e G_e^T b_element[type e] (Eq. 19 assembled), D = sum_e G_e^T
+// diag(A_element[type e]); constrained DOFs and lattice holes get b = 0, D^-1 = 0.
+__global__ void __launch_bounds__(kThreads) k_rhs_diag(const __grid_constant__ RhsArgs a) {
+    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+        const VecWork it = a.vwork[w];
+        const ArrayDev A = a.arrays[it.array];
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
+            int comp, gx, gy, gz;
+            lattice_coords(A, g, comp, gx, gy, gz);
+            double bs = 0, ds = 0;
+            for_owners(A, a.lm->surf_idx, a.lm->n, gx, gy, gz, [&](long long blk, int s) {
+                int t = a.site[blk];
+                int k = 3 * s + comp;
+                bs += a.tt.br[t][k];
+                ds += a.tt.Kr[t][(size_t)k * a.m + k];
+            });
+            bool fixed = (A.clamp_bottom && gz == 0) || (A.clamp_top && gz == A.Z - 1) ||
+                         (a.fixed && a.fixed[g]) || ds == 0.0;
+            a.b[g] = fixed ? 0.0 : A.dT * bs;
+            a.dinv[g] = fixed ? 0.0 : 1.0 / ds;
+        }
+    }
+}
+
+// ------------------------------------------------------ a3: operator apply
+struct ApplyArgs {
+    const ApplyWork* work;
+    int n_work;
+    const int* blist;
+    const BlockRef* bref;
+    const ArrayDev* arrays;
+    const LocalMap* lm;
+    const PcgState* st;    // optional: skip arrays that stopped
+    TypeTab tt;
+    int m, ldY;
+    const void* x;
+    void* Y;
+};
+
+// Shared part of the gather: per-tile lattice base of each block and the
+// per-array offset of each element DOF.
+__device__ __forceinline__ void tile_setup(const ApplyArgs& a, const ApplyWork& it, const ArrayDev& A, long long* base,
+                                           int* offs) {
+    const int n1 = a.lm->n - 1;
+    for (int k = threadIdx.x; k < a.m; k += kThreads) {
+        int q = k / 3, c = k - 3 * q;
+        offs[k] = ((a.lm->qc[q] * A.Y + a.lm->qb[q]) * A.X + a.lm->qa[q]) * 3 + c;
+    }
+    if (threadIdx.x < kTile64 && threadIdx.x < it.count) {
+        BlockRef br = a.bref[a.blist[it.start + threadIdx.x]];
+        base[threadIdx.x] = A.vec_off + 3LL * ((long long)br.j * n1 * A.X + (long long)br.i * n1);
+    }
+}
+
+// FP64 element products, tiles of 32 blocks of one type and one array.
+// Shared: C [m][32] (gathered coefficients), K panel [8*RPT][m].
+template <int RPT>
+__global__ void __launch_bounds__(kThreads) k_apply64(const __grid_constant__ ApplyArgs a) {
+    extern __shared__ double sm[];
+    __shared__ long long base[kTile64];
+    __shared__ int offs[3 * kMaxSurf];
+    const int m = a.m;
+    double* Cs = sm;
+    double* Ks = sm + (size_t)m * kTile64;
+    const double* __restrict__ x = static_cast<const double*>(a.x);
+    double* __restrict__ Y = static_cast<double*>(a.Y);
+    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
+        const ApplyWork it = a.work[w];
+        if (a.st && !a.st[it.array].active) continue;
+        const ArrayDev A = a.arrays[it.array];
+        __syncthreads();
+        tile_setup(a, it, A, base, offs);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m * kTile64; idx += kThreads) {
+            int k = idx >> 5, bt = idx & 31;
+            Cs[idx] = bt < it.count ? x[base[bt] + offs[k]] : 0.0;
+        }
+        const double* __restrict__ K = a.tt.Kr[it.type];
+        const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
+        for (int r0 = 0; r0 < m; r0 += 8 * RPT) {
+            __syncthreads();
+            const int rows = min(8 * RPT, m - r0);
+            for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += kThreads)
+                Ks[idx] = idx < rows * m ? K[(size_t)r0 * m + idx] : 0.0;
+            __syncthreads();
+            double acc[RPT];
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) acc[u] = 0;
+            const double* kr = Ks + rg * RPT * m;
+            for (int k = 0; k < m; ++k) {
+                double c = Cs[k * kTile64 + bt];
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) acc[u] = fma(kr[u * m + k], c, acc[u]);
+            }
+            if (bt < it.count) {
+                const long long e = a.blist[it.start + bt];
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) {
+                    int r = r0 + rg * RPT + u;
+                    if (r < m) Y[e * a.ldY + r] = acc[u];
+                }
+            }
+        }
+    }
+}
+
+// Reduced-precision element products on CUDA cores (FP32 vectors). The
+// operator copy Klp holds K rounded to the mode's operand format (stored as
+// float); BF16X3 holds [K_hi; K_lo]. The gathered coefficients are rounded the
+// same way and products accumulate in FP32, as on the tensor cores.
+__device__ __forceinline__ float round_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+template <int RPT, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply32(const __grid_constant__ ApplyArgs a) {
+    extern __shared__ float smf[];
+    __shared__ long long base[kTile64];
+    __shared__ int offs[3 * kMaxSurf];
+    const int m = a.m;
+    constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
+    float* Cs = smf;                                   // [NS][m][32]
+    float* Ks = smf + (size_t)NS * m * kTile64;        // [NS][8*RPT][m]
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    float* __restrict__ Y = static_cast<float*>(a.Y);
+    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
+        const ApplyWork it = a.work[w];
+        if (a.st && !a.st[it.array].active) continue;
+        const ArrayDev A = a.arrays[it.array];
+        __syncthreads();
+        tile_setup(a, it, A, base, offs);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m * kTile64; idx += kThreads) {
+            int k = idx >> 5, bt = idx & 31;
+            float v = bt < it.count ? x[base[bt] + offs[k]] : 0.0f;
+            if (MODE == MSTRESS_TF32) Cs[idx] = round_tf32(v);
+            else if (MODE == MSTRESS_BF16) Cs[idx] = round_bf16(v);
+            else {
+                float hi = round_bf16(v);
+                Cs[idx] = hi;
+                Cs[(size_t)m * kTile64 + idx] = round_bf16(v - hi);
+            }
+        }
+        const float* __restrict__ K = static_cast<const float*>(a.tt.Klp[it.type]);
+        const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
+        for (int r0 = 0; r0 < m; r0 += 8 * RPT) {
+            __syncthreads();
+            const int rows = min(8 * RPT, m - r0);
+            for (int s = 0; s < NS; ++s)
+                for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += kThreads)
+                    Ks[(size_t)s * 8 * RPT * m + idx] =
+                        idx < rows * m ? K[(size_t)s * m * m + (size_t)r0 * m + idx] : 0.0f;
+            __syncthreads();
+            float acc[RPT];
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) acc[u] = 0;
+            const float* kr = Ks + rg * RPT * m;
+            for (int k = 0; k < m; ++k) {
+                float c = Cs[k * kTile64 + bt];
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) acc[u] = fmaf(kr[u * m + k], c, acc[u]);
+                if (NS == 2) {
+                    float cl = Cs[(size_t)m * kTile64 + k * kTile64 + bt];
+                    const float* krl = kr + (size_t)8 * RPT * m;
+#pragma unroll
+                    for (int u = 0; u < RPT; ++u) acc[u] = fmaf(kr[u * m + k], cl, fmaf(krl[u * m + k], c, acc[u]));
+                }
+            }
+            if (bt < it.count) {
+                const long long e = a.blist[it.start + bt];
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) {
+                    int r = r0 + rg * RPT + u;
+                    if (r < m) Y[e * a.ldY + r] = acc[u];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------- a3: interface sum
+struct IsumArgs {
+    const VecWork* vwork;
+    int n_vwork;
+    const ArrayDev* arrays;
+    const LocalMap* lm;
+    const PcgState* st;     // optional: skip stopped arrays
+    const double* dinv;     // optional: zero the constrained rows
+    int ldY;
+    const void* Y;
+    const void* p;
+    void* q;
+    double* part_pq;        // optional
+};
+
+// q_g = sum over owning blocks of Y_e[local DOF] (owner computes, fixed order).
+template <class V, class YT>
+__global__ void __launch_bounds__(kThreads) k_isum(const __grid_constant__ IsumArgs a) {
+    __shared__ double sh[kThreads / 32];
+    const YT* __restrict__ Y = static_cast<const YT*>(a.Y);
+    const V* __restrict__ p = static_cast<const V*>(a.p);
+    V* __restrict__ q = static_cast<V*>(a.q);
+    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+        const VecWork it = a.vwork[w];
+        if (a.st && !a.st[it.array].active) continue;
+        const ArrayDev A = a.arrays[it.array];
+        double acc = 0;
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
+            double s = 0;
+            if (!a.dinv || a.dinv[g] != 0.0) {
+                int comp, gx, gy, gz;
+                lattice_coords(A, g, comp, gx, gy, gz);
+                for_owners(A, a.lm->surf_idx, a.lm->n, gx, gy, gz, [&](long long blk, int sidx) {
+                    s += (double)Y[blk * a.ldY + 3 * sidx + comp];
+                });
+            }
+            q[g] = (V)s;
+            acc += (double)p[g] * s;
+        }
+        if (a.part_pq) {
+            double t = block_sum(acc, sh);
+            if (threadIdx.x == 0) a.part_pq[w] = t;
+        }
+    }
+}
+
+// ------------------------------------------------------- a4: PCG vectors
+struct VecArgs {
+    const VecWork* vwork;
+    int n_vwork;
+    const ArrayDev* arrays;
+    PcgState* st;
+    const double* dinv;
+    void *x, *r, *z, *p, *q;
+    const void* rhs;        // init: right-hand side (FP64)
+    double *part_pq, *part_rz, *part_rr;
+};
+
+template <class V>
+__global__ void __launch_bounds__(kThreads) k_pcg_init(const __grid_constant__ VecArgs a) {
+    __shared__ double sh[kThreads / 32];
+    V *x = (V*)a.x, *r = (V*)a.r, *z = (V*)a.z, *p = (V*)a.p;
+    const double* rhs = (const double*)a.rhs;
+    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+        const VecWork it = a.vwork[w];
+        double srz = 0, srr = 0;
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
+            double d = a.dinv[g];
+            V rv = d != 0.0 ? (V)rhs[g] : (V)0;
+            V zv = (V)(d * (double)rv);
+            x[g] = (V)0;
+            r[g] = rv;
+            z[g] = zv;
+            p[g] = zv;
+            srz += (double)rv * (double)zv;
+            srr += (double)rv * (double)rv;
+        }
+        srz = block_sum(srz, sh);
+        srr = block_sum(srr, sh);
+        if (threadIdx.x == 0) { a.part_rz[w] = srz; a.part_rr[w] = srr; }
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(kThreads) k_vec1(const __grid_constant__ VecArgs a) {
+    __shared__ double sh[kThreads / 32];
+    __shared__ double s_alpha;
+    V *x = (V*)a.x, *r = (V*)a.r, *z = (V*)a.z;
+    const V *p = (const V*)a.p, *q = (const V*)a.q;
+    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+        const VecWork it = a.vwork[w];
+        const PcgState st = a.st[it.array];
+        if (!st.active) continue;
+        const ArrayDev A = a.arrays[it.array];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double pq = warp_fold(a.part_pq + A.vwork_off, A.n_vwork);
+            double al = st.rz / pq;
+            if (threadIdx.x == 0) s_alpha = (pq > 0 && isfinite(al)) ? al : 0.0;
+        }
+        __syncthreads();
+        const double al = s_alpha;
+        double srz = 0, srr = 0;
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
+            double pv = (double)p[g], qv = (double)q[g];
+            x[g] = (V)((double)x[g] + al * pv);
+            V rv = (V)((double)r[g] - al * qv);
+            V zv = (V)(a.dinv[g] * (double)rv);
+            r[g] = rv;
+            z[g] = zv;
+            srz += (double)rv * (double)zv;
+            srr += (double)rv * (double)rv;
+        }
+        srz = block_sum(srz, sh);
+        srr = block_sum(srr, sh);
+        if (threadIdx.x == 0) { a.part_rz[w] = srz; a.part_rr[w] = srr; }
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(kThreads) k_vec2(const __grid_constant__ VecArgs a) {
+    __shared__ double s_beta;
+    const V* z = (const V*)a.z;
+    V* p = (V*)a.p;
+    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+        const VecWork it = a.vwork[w];
+        const PcgState st = a.st[it.array];
+        if (!st.active) continue;
+        const ArrayDev A = a.arrays[it.array];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
+            if (threadIdx.x == 0) s_beta = rz / st.rz;
+        }
+        __syncthreads();
+        const double be = s_beta;
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads)
+            p[g] = (V)((double)z[g] + be * (double)p[g]);
+    }
+}
+
+// a5: r = b - q on free DOFs (FP64 residual of the outer refinement loop),
+// and its partial <r, r>.
+__global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ VecArgs a) {
+    __shared__ double sh[kThreads / 32];
+    const double* b = (const double*)a.rhs;
+    const double* q = (const double*)a.q;
+    double* r = (double*)a.r;
+    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+        const VecWork it = a.vwork[w];
+        double srr = 0;
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
+            double rv = a.dinv[g] != 0.0 ? b[g] - q[g] : 0.0;
+            r[g] = rv;
+            srr += rv * rv;
+        }
+        srr = block_sum(srr, sh);
+        if (threadIdx.x == 0) a.part_rr[w] = srr;
+    }
+}
+
+// x64 += d32 for arrays still refining.
+__global__ void __launch_bounds__(kThreads) k_correct(const VecWork* vwork, int n_vwork, const PcgState* outer,
+                                                      double* x, const float* d) {
+    for (int w = blockIdx.x; w < n_vwork; w += gridDim.x) {
+        const VecWork it = vwork[w];
+        if (!outer[it.array].active) continue;
+        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) x[g] += (double)d[g];
+    }
+}
+
+__global__ void k_add_bc(long long n, double* x, const double* xbc) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) x[i] += xbc[i];
+}
+
+__global__ void k_lift_rhs(long long n, double* b, const double* Axbc, const double* dinv) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n && dinv[i] != 0.0) b[i] -= Axbc[i];
+}
+
+// ----------------------------------------------------- a4: scalar phase
+struct ScalarArgs {
+    int n_arrays;
+    const ArrayDev* arrays;
+    PcgState* st;
+    const double *part_pq, *part_rz, *part_rr;
+    int* any;
+    int mode;         // 0: iteration, 1: PCG start (tol from rtol), 2: outer residual check
+    double rtol;
+    int max_iter;
+    const PcgState* gate;   // mode 1: only arrays active here start (may be NULL)
+};
+
+__global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ ScalarArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int any = 0;
+    for (int k = warp; k < a.n_arrays; k += 32) {
+        const ArrayDev A = a.arrays[k];
+        PcgState s = a.st[k];
+        if (a.mode == 0) {
+            if (!s.active) continue;
+            double pq = warp_fold(a.part_pq + A.vwork_off, A.n_vwork);
+            double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
+            double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
+            if (lane == 0) {
+                s.iters += 1;
+                if (!(pq > 0) || !isfinite(rz) || !isfinite(rr)) {
+                    s.active = 0;
+                    s.status = MSTRESS_ENUMERIC;
+                } else {
+                    s.rz = rz;
+                    s.rr = rr;
+                    if (rr <= s.tol2) { s.active = 0; s.status = MSTRESS_OK; }
+                    else if (s.iters >= s.max_iter) { s.active = 0; s.status = MSTRESS_ENOT_CONVERGED; }
+                }
+                a.st[k] = s;
+            }
+        } else if (a.mode == 1) {
+            double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
+            double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
+            if (lane == 0) {
+                bool gate = a.gate ? a.gate[k].active != 0 : true;
+                s.rz = rz;
+                s.rr = rr;
+                s.bb = rr;
+                s.tol2 = a.rtol * a.rtol * rr;
+                s.iters = 0;
+                s.max_iter = a.max_iter;
+                s.status = MSTRESS_OK;
+                s.active = (gate && rr > 0 && isfinite(rr)) ? 1 : 0;
+                if (!isfinite(rr)) s.status = MSTRESS_ENUMERIC;
+                a.st[k] = s;
+            }
+        } else {   // outer check: part_rr holds ||b - A x||^2 partials; s.bb = ||b||^2
+            double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
+            if (lane == 0) {
+                s.rr = rr;
+                if (s.active) {
+                    if (!isfinite(rr)) { s.active = 0; s.status = MSTRESS_ENUMERIC; }
+                    else if (rr <= a.rtol * a.rtol * s.bb) { s.active = 0; s.status = MSTRESS_OK; }
+                    else if (s.iters >= s.max_iter) { s.active = 0; s.status = MSTRESS_ENOT_CONVERGED; }
+                    else s.iters += 1;
+                }
+                a.st[k] = s;
+            }
+        }
+        if (lane == 0) any |= a.st[k].active;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0 && a.any) *a.any = any;
+}
+
+// ------------------------------------------------------------ launches
+int grid_for(mstress_sol_s* s, int items, int per_sm) {
+    return std::max(1, std::min(items, s->ctx->num_sms * per_sm));
+}
+
+ApplyArgs apply_args(mstress_sol_s* s, const void* x, const PcgState* st, void* Y) {
+    ApplyArgs a;
+    a.work = s->d_awork.as<ApplyWork>();
+    a.n_work = s->n_awork;
+    a.blist = s->d_blist.as<int>();
+    a.bref = s->d_bref.as<BlockRef>();
+    a.arrays = s->d_arrays.as<ArrayDev>();
+    a.lm = s->d_lm.as<LocalMap>();
+    a.st = st;
+    a.tt = s->tt;
+    a.m = s->m;
+    a.ldY = s->ldY;
+    a.x = x;
+    a.Y = Y;
+    return a;
+}
+
+constexpr int kMaxDynSmem = 200 * 1024;
+
+// Raise the dynamic shared-memory limit of every apply kernel once per device
+// (outside any stream capture).
+void configure_apply_kernels(int device) {
+    static bool done[64] = {};
+    if (device < 0 || device >= 64 || done[device]) return;
+    auto set = [](auto k) { MS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)); };
+    set(k_apply64<10>);
+    set(k_apply64<4>);
+    set(k_apply32<10, MSTRESS_TF32>);
+    set(k_apply32<10, MSTRESS_BF16>);
+    set(k_apply32<10, MSTRESS_BF16X3>);
+    set(k_apply32<4, MSTRESS_TF32>);
+    set(k_apply32<4, MSTRESS_BF16>);
+    set(k_apply32<4, MSTRESS_BF16X3>);
+    done[device] = true;
+}
+
+template <class KER>
+void launch_with_smem(KER kernel, mstress_sol_s* s, size_t smem, const ApplyArgs& a) {
+    MS_REQUIRE(smem <= (size_t)kMaxDynSmem, MSTRESS_EINVAL, "apply tile does not fit in shared memory");
+    int per_sm = smem > 110 * 1024 ? 1 : (smem > 70 * 1024 ? 2 : 3);
+    kernel<<<grid_for(s, a.n_work, per_sm), kThreads, smem, s->ctx->stream>>>(a);
+    MS_LAUNCH_CHECK();
+}
+
+VecArgs vec_args(mstress_sol_s* s, PcgVectors& v) {
+    VecArgs a;
+    a.vwork = s->d_vwork.as<VecWork>();
+    a.n_vwork = s->n_vwork;
+    a.arrays = s->d_arrays.as<ArrayDev>();
+    a.st = v.state.as<PcgState>();
+    a.dinv = s->dinv.as<double>();
+    a.x = v.x.ptr;
+    a.r = v.r.ptr;
+    a.z = v.z.ptr;
+    a.p = v.p.ptr;
+    a.q = v.q.ptr;
+    a.rhs = nullptr;
+    a.part_pq = s->part.as<double>();
+    a.part_rz = a.part_pq + s->n_vwork;
+    a.part_rr = a.part_rz + s->n_vwork;
+    return a;
+}
+
+ScalarArgs scalar_args(mstress_sol_s* s, PcgVectors& v, int mode, double rtol, int max_iter, const PcgState* gate) {
+    ScalarArgs a;
+    a.n_arrays = s->n_arrays;
+    a.arrays = s->d_arrays.as<ArrayDev>();
+    a.st = v.state.as<PcgState>();
+    a.part_pq = s->part.as<double>();
+    a.part_rz = a.part_pq + s->n_vwork;
+    a.part_rr = a.part_rz + s->n_vwork;
+    a.any = s->flag.as<int>();
+    a.mode = mode;
+    a.rtol = rtol;
+    a.max_iter = max_iter;
+    a.gate = gate;
+    return a;
+}
+
+}  // namespace
+
+void launch_apply(mstress_sol_s* s, int prec, const void* x, bool vec_fp32, const PcgState* st, void* Y) {
+    ApplyArgs a = apply_args(s, x, st, Y);
+    const int m = s->m;
+    if (prec == MSTRESS_FP64) {
+        MS_REQUIRE(!vec_fp32, MSTRESS_EINVAL, "FP64 apply needs FP64 vectors");
+        if (m <= 80) launch_with_smem(k_apply64<10>, s, (size_t)(m * kTile64 + 80 * m) * sizeof(double), a);
+        else launch_with_smem(k_apply64<4>, s, (size_t)(m * kTile64 + 32 * m) * sizeof(double), a);
+        return;
+    }
+    MS_REQUIRE(vec_fp32, MSTRESS_EINVAL, "reduced-precision apply needs FP32 vectors");
+    const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
+    if (m <= 80) {
+        size_t smem = (size_t)ns * (m * kTile64 + 80 * m) * sizeof(float);
+        if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<10, MSTRESS_TF32>, s, smem, a);
+        else if (prec == MSTRESS_BF16) launch_with_smem(k_apply32<10, MSTRESS_BF16>, s, smem, a);
+        else launch_with_smem(k_apply32<10, MSTRESS_BF16X3>, s, smem, a);
+    } else {
+        size_t smem = (size_t)ns * (m * kTile64 + 32 * m) * sizeof(float);
+        if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<4, MSTRESS_TF32>, s, smem, a);
+        else if (prec == MSTRESS_BF16) launch_with_smem(k_apply32<4, MSTRESS_BF16>, s, smem, a);
+        else launch_with_smem(k_apply32<4, MSTRESS_BF16X3>, s, smem, a);
+    }
+}
+
+void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, const void* p, void* q, bool vec_fp32,
+                 const double* dinv, const PcgState* st, double* part_pq) {
+    IsumArgs a;
+    a.vwork = s->d_vwork.as<VecWork>();
+    a.n_vwork = s->n_vwork;
+    a.arrays = s->d_arrays.as<ArrayDev>();
+    a.lm = s->d_lm.as<LocalMap>();
+    a.st = st;
+    a.dinv = dinv;
+    a.ldY = s->ldY;
+    a.Y = Y;
+    a.p = p;
+    a.q = q;
+    a.part_pq = part_pq;
+    int g = grid_for(s, s->n_vwork, 8);
+    cudaStream_t stream = s->ctx->stream;
+    if (!vec_fp32 && !y_fp32) k_isum<double, double><<<g, kThreads, 0, stream>>>(a);
+    else if (vec_fp32 && y_fp32) k_isum<float, float><<<g, kThreads, 0, stream>>>(a);
+    else if (!vec_fp32 && y_fp32) k_isum<double, float><<<g, kThreads, 0, stream>>>(a);
+    else MS_REQUIRE(false, MSTRESS_EINVAL, "unsupported isum types");
+    MS_LAUNCH_CHECK();
+}
+
+namespace {
+
+// One PCG iteration over all arrays (five launches), on vectors v of type V.
+template <class V>
+void pcg_iteration(mstress_sol_s* s, PcgVectors& v, int prec) {
+    constexpr bool f32 = std::is_same<V, float>::value;
+    cudaStream_t stream = s->ctx->stream;
+    const PcgState* st = v.state.as<PcgState>();
+    launch_apply(s, prec, v.p.ptr, f32, st, s->Y.ptr);
+    launch_isum(s, s->Y.ptr, f32, v.p.ptr, v.q.ptr, f32, s->dinv.as<double>(), st, s->part.as<double>());
+    VecArgs va = vec_args(s, v);
+    int g = grid_for(s, s->n_vwork, 8);
+    k_vec1<V><<<g, kThreads, 0, stream>>>(va);
+    MS_LAUNCH_CHECK();
+    k_vec2<V><<<g, kThreads, 0, stream>>>(va);
+    MS_LAUNCH_CHECK();
+    ScalarArgs sa = scalar_args(s, v, 0, 0, 0, nullptr);
+    k_scalars<<<1, 1024, 0, stream>>>(sa);
+    MS_LAUNCH_CHECK();
+}
+
+// Start a PCG run on right-hand side rhs (FP64 device vector): x = 0, r = rhs
+// on free DOFs, z = D^-1 r, p = z; tolerance rtol relative to ||rhs||.
+template <class V>
+void pcg_start(mstress_sol_s* s, PcgVectors& v, const double* rhs, double rtol, int max_iter, const PcgState* gate) {
+    cudaStream_t stream = s->ctx->stream;
+    VecArgs va = vec_args(s, v);
+    va.rhs = rhs;
+    k_pcg_init<V><<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
+    MS_LAUNCH_CHECK();
+    ScalarArgs sa = scalar_args(s, v, 1, rtol, max_iter, gate);
+    k_scalars<<<1, 1024, 0, stream>>>(sa);
+    MS_LAUNCH_CHECK();
+}
+
+constexpr int kGraphIters = 16;
+
+// Iterate until every array has stopped: replay a captured graph of
+// kGraphIters iterations, polling the device any-active flag between replays.
+template <class V>
+void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
+    constexpr int gi = std::is_same<V, float>::value ? 1 : 0;
+    cudaStream_t stream = s->ctx->stream;
+    if (stream == nullptr) {   // the legacy default stream cannot be captured: launch directly
+        for (int done_iters = 0; done_iters < max_iter; done_iters += kGraphIters) {
+            for (int k = 0; k < kGraphIters; ++k) pcg_iteration<V>(s, v, prec);
+            MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+            MS_CUDA(cudaStreamSynchronize(stream));
+            if (s->ctx->h_flag[0] == 0) break;
+        }
+        return;
+    }
+    if (!s->graph[gi]) {
+        cudaGraph_t g;
+        MS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        g_capturing = true;
+        try {
+            for (int k = 0; k < kGraphIters; ++k) pcg_iteration<V>(s, v, prec);
+        } catch (...) {
+            g_capturing = false;
+            cudaStreamEndCapture(stream, &g);
+            throw;
+        }
+        g_capturing = false;
+        MS_CUDA(cudaStreamEndCapture(stream, &g));
+        size_t n_nodes = 0;
+        cudaGraphGetNodes(g, nullptr, &n_nodes);
+        s->graph_iters[gi] = (int)n_nodes;    // kernel nodes per replay
+        cudaError_t e = cudaGraphInstantiate(&s->graph[gi], g, 0);
+        cudaGraphDestroy(g);
+        MS_CUDA(e);
+    }
+    int done_iters = 0;
+    // first check after a short burst: small arrays converge in few iterations
+    while (done_iters < max_iter) {
+        MS_CUDA(cudaGraphLaunch(s->graph[gi], stream));
+        note_launches(s->graph_iters[gi]);
+        done_iters += kGraphIters;
+        MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        MS_CUDA(cudaStreamSynchronize(stream));
+        if (s->ctx->h_flag[0] == 0) break;
+    }
+}
+
+// FP64 residual r = b - A x (a5) and the outer stopping test; returns whether
+// any array still needs a refinement step.
+bool outer_check(mstress_sol_s* s, int max_outer) {
+    cudaStream_t stream = s->ctx->stream;
+    PcgVectors& v = s->v64;
+    launch_apply(s, MSTRESS_FP64, v.x.ptr, false, nullptr, s->Y.ptr);
+    launch_isum(s, s->Y.ptr, false, v.x.ptr, v.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
+    VecArgs va = vec_args(s, v);
+    va.rhs = s->b.ptr;
+    k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
+    MS_LAUNCH_CHECK();
+    ScalarArgs sa = scalar_args(s, v, 2, s->ctx->opts.rtol, max_outer, nullptr);
+    k_scalars<<<1, 1024, 0, stream>>>(sa);
+    MS_LAUNCH_CHECK();
+    MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(cudaStreamSynchronize(stream));
+    return s->ctx->h_flag[0] != 0;
+}
+
+// -------------------------------------------------------- solve set-up
+struct LayoutIn {
+    const mstress_layout* L;
+    double dT;
+    const mstress_bc* bc;
+};
+
+void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
+    mstress_ctx ctx = s->ctx;
+    // block models -> type table
+    for (auto& li : in) {
+        const mstress_layout* L = li.L;
+        MS_REQUIRE(L, MSTRESS_EINVAL, "layout is NULL");
+        MS_REQUIRE(L->nx >= 1 && L->ny >= 1, MSTRESS_EINVAL, "array needs nx, ny >= 1");
+        MS_REQUIRE((int64_t)L->nx * L->ny <= (1 << 26), MSTRESS_EINVAL, "array too large");
+        MS_REQUIRE(L->site_type && L->blocks && L->n_blocks >= 1, MSTRESS_EINVAL, "layout needs site_type and blocks");
+        MS_REQUIRE(std::isfinite(li.dT), MSTRESS_EINVAL, "dT must be finite");
+        for (int k = 0; k < L->n_blocks; ++k) {
+            mstress_block b = L->blocks[k];
+            MS_REQUIRE(b && b->ctx == ctx, MSTRESS_EINVAL, "block is NULL or from another context");
+            if (std::find(s->types.begin(), s->types.end(), b) == s->types.end()) s->types.push_back(b);
+        }
+        for (int k = 1; k < L->n_blocks; ++k) {
+            mstress_block a = L->blocks[0], b = L->blocks[k];
+            MS_REQUIRE(a->lx == b->lx && a->ly == b->ly && a->lz == b->lz, MSTRESS_EINVAL,
+                       "blocks of one array must share their dimensions");
+        }
+        for (int64_t k = 0; k < (int64_t)L->nx * L->ny; ++k)
+            MS_REQUIRE(L->site_type[k] < L->n_blocks, MSTRESS_EINVAL, "site_type out of range");
+        const mstress_bc* bc = li.bc;
+        if (bc) {
+            MS_REQUIRE(bc->n_prescribed == 0 || (bc->prescribed_dof && bc->prescribed_val), MSTRESS_EINVAL,
+                       "prescribed arrays are NULL");
+            MS_REQUIRE(bc->clamp_bottom || bc->clamp_top || bc->n_prescribed > 0, MSTRESS_EINVAL,
+                       "no constrained DOF: the reduced system is singular (rigid motions)");
+        }
+    }
+    MS_REQUIRE((int)s->types.size() <= kMaxTypes, MSTRESS_EINVAL, "too many block models in one solve");
+    s->n_types = (int)s->types.size();
+    mstress_block t0 = s->types[0];
+    for (auto b : s->types)
+        MS_REQUIRE(b->n == t0->n && b->n_el == t0->n_el && b->n_dof == t0->n_dof, MSTRESS_EINVAL,
+                   "all block models of a solve need the same basis order and mesh size");
+    s->n = t0->n;
+    s->m = t0->m;
+    s->ldY = (int)round_up(s->m, 16);
+    configure_apply_kernels(ctx->device);
+    s->n_el = t0->n_el;
+    s->n_dof_block = t0->n_dof;
+    LocalMap lm = make_local_map(s->n);
+    s->n_arrays = (int)in.size();
+    const int n1 = s->n - 1;
+
+    std::vector<BlockRef> bref;
+    std::vector<VecWork> vwork;
+    std::vector<ApplyWork> awork;
+    std::vector<int> blist;
+    std::vector<uint8_t> fixed;
+    std::vector<double> xbc;
+    bool any_presc = false;
+    for (auto& li : in)
+        if (li.bc && li.bc->n_prescribed) any_presc = true;
+    int64_t vec_off = 0, block_off = 0;
+    for (int a = 0; a < s->n_arrays; ++a) {
+        const mstress_layout* L = in[a].L;
+        ArrayDev A{};
+        A.nx = L->nx;
+        A.ny = L->ny;
+        A.X = L->nx * n1 + 1;
+        A.Y = L->ny * n1 + 1;
+        A.Z = s->n;
+        A.clamp_bottom = in[a].bc ? in[a].bc->clamp_bottom : 1;
+        A.clamp_top = in[a].bc ? in[a].bc->clamp_top : 0;
+        A.vec_off = vec_off;
+        A.n_dof = 3LL * A.X * A.Y * A.Z;
+        A.block_off = block_off;
+        A.dT = in[a].dT;
+        A.vwork_off = (int)vwork.size();
+        for (int64_t st = 0; st < A.n_dof; st += kVecChunk)
+            vwork.push_back(VecWork{a, 0, vec_off + st, std::min<int64_t>(kVecChunk, A.n_dof - st)});
+        A.n_vwork = (int)vwork.size() - A.vwork_off;
+        // type index of each site
+        std::vector<int> tmap(L->n_blocks);
+        for (int k = 0; k < L->n_blocks; ++k)
+            tmap[k] = (int)(std::find(s->types.begin(), s->types.end(), L->blocks[k]) - s->types.begin());
+        std::vector<std::vector<int>> per_type(s->n_types);
+        for (int j = 0; j < L->ny; ++j)
+            for (int i = 0; i < L->nx; ++i) {
+                int t = tmap[L->site_type[(int64_t)j * L->nx + i]];
+                int64_t e = block_off + (int64_t)j * L->nx + i;
+                bref.push_back(BlockRef{a, i, j, t});
+                s->site.push_back((uint8_t)t);
+                per_type[t].push_back((int)e);
+            }
+        for (int t = 0; t < s->n_types; ++t) {
+            auto& v = per_type[t];
+            for (size_t st = 0; st < v.size(); st += kTile64) {
+                int cnt = (int)std::min<size_t>(kTile64, v.size() - st);
+                awork.push_back(ApplyWork{t, a, (int)blist.size(), cnt});
+                for (int k = 0; k < cnt; ++k) blist.push_back(v[st + k]);
+            }
+        }
+        if (any_presc) {
+            fixed.resize(vec_off + A.n_dof, 0);
+            xbc.resize(vec_off + A.n_dof, 0.0);
+            const mstress_bc* bc = in[a].bc;
+            if (bc)
+                for (size_t k = 0; k < bc->n_prescribed; ++k) {
+                    int64_t d = bc->prescribed_dof[k];
+                    MS_REQUIRE(d >= 0 && d < A.n_dof, MSTRESS_EINVAL, "prescribed DOF out of range");
+                    MS_REQUIRE(std::isfinite(bc->prescribed_val[k]), MSTRESS_EINVAL, "prescribed value not finite");
+                    fixed[vec_off + d] = 1;
+                    xbc[vec_off + d] = bc->prescribed_val[k];
+                }
+        }
+        s->arrays.push_back(A);
+        vec_off += A.n_dof;
+        block_off += (int64_t)L->nx * L->ny;
+    }
+    s->n_vec = vec_off;
+    s->n_blocks = block_off;
+    MS_REQUIRE(s->n_blocks < (1LL << 31), MSTRESS_EINVAL, "too many blocks");
+    s->n_vwork = (int)vwork.size();
+    s->n_awork = (int)awork.size();
+
+    cudaStream_t st = ctx->stream;
+    auto up = [&](DBuf& d, const void* src, size_t bytes) {
+        alloc_into(ctx, d, bytes, false);
+        MS_CUDA(cudaMemcpyAsync(d.ptr, src, bytes, cudaMemcpyHostToDevice, st));
+    };
+    up(s->d_lm, &lm, sizeof(LocalMap));
+    up(s->d_arrays, s->arrays.data(), s->arrays.size() * sizeof(ArrayDev));
+    up(s->d_bref, bref.data(), bref.size() * sizeof(BlockRef));
+    up(s->d_blist, blist.data(), blist.size() * sizeof(int));
+    up(s->d_awork, awork.data(), awork.size() * sizeof(ApplyWork));
+    up(s->d_vwork, vwork.data(), vwork.size() * sizeof(VecWork));
+    up(s->d_site, s->site.data(), s->site.size());
+    if (any_presc) {
+        up(s->fixed, fixed.data(), fixed.size());
+        up(s->xbc, xbc.data(), xbc.size() * sizeof(double));
+    }
+    for (int t = 0; t < s->n_types; ++t) {
+        s->tt.Kr[t] = s->types[t]->Kr.as<double>();
+        s->tt.br[t] = s->types[t]->br.as<double>();
+    }
+    const size_t nv = (size_t)s->n_vec;
+    alloc_into(ctx, s->b, nv * sizeof(double), false);
+    alloc_into(ctx, s->dinv, nv * sizeof(double), false);
+    alloc_into(ctx, s->v64.x, nv * sizeof(double));
+    alloc_into(ctx, s->v64.r, nv * sizeof(double), false);
+    alloc_into(ctx, s->v64.z, nv * sizeof(double), false);
+    alloc_into(ctx, s->v64.p, nv * sizeof(double), false);
+    alloc_into(ctx, s->v64.q, nv * sizeof(double), false);
+    alloc_into(ctx, s->v64.state, s->n_arrays * sizeof(PcgState));
+    alloc_into(ctx, s->part, 3 * (size_t)s->n_vwork * sizeof(double));
+    alloc_into(ctx, s->flag, 64);
+    const bool mixed = s->precision != MSTRESS_FP64;
+    alloc_into(ctx, s->Y, (size_t)s->n_blocks * s->ldY * (mixed ? sizeof(float) : sizeof(double)), false);
+    if (mixed) {
+        // the FP64 residual needs an FP64 element buffer of its own
+        for (int t = 0; t < s->n_types; ++t) {
+            ensure_lowp(s->types[t], s->precision);
+            s->tt.Klp[t] = s->types[t]->Kr_lp[s->precision].ptr;
+        }
+        alloc_into(ctx, s->v32.x, nv * sizeof(float));
+        alloc_into(ctx, s->v32.r, nv * sizeof(float), false);
+        alloc_into(ctx, s->v32.z, nv * sizeof(float), false);
+        alloc_into(ctx, s->v32.p, nv * sizeof(float), false);
+        alloc_into(ctx, s->v32.q, nv * sizeof(float), false);
+        alloc_into(ctx, s->v32.state, s->n_arrays * sizeof(PcgState));
+    }
+}
+
+void run_solve(mstress_sol_s* s) {
+    mstress_ctx ctx = s->ctx;
+    cudaStream_t stream = ctx->stream;
+    const mstress_opts& o = ctx->opts;
+    const bool mixed = s->precision != MSTRESS_FP64;
+    // a2: right-hand side and Jacobi diagonal
+    RhsArgs ra;
+    ra.vwork = s->d_vwork.as<VecWork>();
+    ra.n_vwork = s->n_vwork;
+    ra.arrays = s->d_arrays.as<ArrayDev>();
+    ra.lm = s->d_lm.as<LocalMap>();
+    ra.site = s->d_site.as<uint8_t>();
+    ra.fixed = s->fixed.as<uint8_t>();
+    ra.tt = s->tt;
+    ra.m = s->m;
+    ra.b = s->b.as<double>();
+    ra.dinv = s->dinv.as<double>();
+    k_rhs_diag<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(ra);
+    MS_LAUNCH_CHECK();
+    DBuf Yfp64;   // FP64 element buffer for the FP64 operator in mixed modes
+    if (mixed) alloc_into(ctx, Yfp64, (size_t)s->n_blocks * s->ldY * sizeof(double), false);
+    void* Y64 = mixed ? Yfp64.ptr : s->Y.ptr;
+    if (s->xbc.ptr) {   // lifting (Eq. 13): b -= A x_bc on the free DOFs
+        launch_apply(s, MSTRESS_FP64, s->xbc.ptr, false, nullptr, Y64);
+        launch_isum(s, Y64, false, s->xbc.ptr, s->v64.q.ptr, false, nullptr, nullptr, nullptr);
+        k_lift_rhs<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->b.as<double>(),
+                                                                            s->v64.q.as<double>(), s->dinv.as<double>());
+        MS_LAUNCH_CHECK();
+    }
+    if (!mixed) {
+        pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_iter, nullptr);
+        pcg_run<double>(s, s->v64, MSTRESS_FP64, o.max_iter);
+    } else {
+        // a5: FP64-residual iterative refinement around a reduced-precision PCG.
+        // outer state: ||b||^2, x = 0, refinement-step count and limit
+        pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_outer, nullptr);
+        int inner_total = 0;
+        for (int k = 0; k <= o.max_outer; ++k) {
+            std::swap(s->Y, Yfp64);
+            bool more = outer_check(s, o.max_outer);
+            std::swap(s->Y, Yfp64);
+            if (!more) break;
+            pcg_start<float>(s, s->v32, s->v64.r.as<double>(), o.inner_rtol, std::max(1, o.max_iter - inner_total),
+                             s->v64.state.as<PcgState>());
+            pcg_run<float>(s, s->v32, s->precision, o.max_iter);
+            k_correct<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
+                s->d_vwork.as<VecWork>(), s->n_vwork, s->v64.state.as<PcgState>(), s->v64.x.as<double>(),
+                s->v32.x.as<float>());
+            MS_LAUNCH_CHECK();
+            std::vector<PcgState> inner(s->n_arrays);
+            MS_CUDA(cudaMemcpyAsync(inner.data(), s->v32.state.ptr, inner.size() * sizeof(PcgState),
+                                    cudaMemcpyDeviceToHost, stream));
+            MS_CUDA(cudaStreamSynchronize(stream));
+            int mx = 0;
+            for (int a = 0; a < s->n_arrays; ++a) {
+                s->results[a].iters += inner[a].iters;
+                mx = std::max(mx, s->results[a].iters);
+            }
+            inner_total = mx;
+        }
+    }
+    // true FP64 residual of the final iterate (and the outer count)
+    {
+        std::vector<PcgState> before(s->n_arrays);
+        MS_CUDA(cudaMemcpyAsync(before.data(), s->v64.state.ptr, before.size() * sizeof(PcgState),
+                                cudaMemcpyDeviceToHost, stream));
+        MS_CUDA(cudaStreamSynchronize(stream));
+        if (mixed) std::swap(s->Y, Yfp64);
+        launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, false, nullptr, s->Y.ptr);
+        launch_isum(s, s->Y.ptr, false, s->v64.x.ptr, s->v64.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
+        VecArgs va = vec_args(s, s->v64);
+        va.rhs = s->b.ptr;
+        // residual into z (scratch) so r keeps the recursive residual
+        va.r = s->v64.z.ptr;
+        k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
+        MS_LAUNCH_CHECK();
+        if (mixed) std::swap(s->Y, Yfp64);
+        std::vector<double> prr(s->n_vwork);
+        MS_CUDA(cudaMemcpyAsync(prr.data(), va.part_rr, prr.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        MS_CUDA(cudaStreamSynchronize(stream));
+        for (int a = 0; a < s->n_arrays; ++a) {
+            const ArrayDev& A = s->arrays[a];
+            double rr = 0;
+            for (int w = 0; w < A.n_vwork; ++w) rr += prr[A.vwork_off + w];
+            ArrayResult& R = s->results[a];
+            R.rel_res = before[a].bb > 0 ? std::sqrt(rr / before[a].bb) : 0.0;
+            if (mixed) {
+                R.outer = before[a].iters;
+                R.status = before[a].status;
+            } else {
+                R.iters = before[a].iters;
+                R.status = before[a].status;
+            }
+            if (!std::isfinite(R.rel_res)) R.status = MSTRESS_ENUMERIC;
+        }
+    }
+    if (s->xbc.ptr) {
+        k_add_bc<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->v64.x.as<double>(),
+                                                                          s->xbc.as<double>());
+        MS_LAUNCH_CHECK();
+    }
+    MS_CUDA(cudaStreamSynchronize(stream));
+}
+
+int solve_common(mstress_ctx ctx, const std::vector<LayoutIn>& in, mstress_sol* out) {
+    std::unique_ptr<mstress_sol_s> s(new mstress_sol_s());
+    s->ctx = ctx;
+    s->precision = ctx->opts.precision;
+    validate_and_build(s.get(), in);
+    s->results.assign(s->n_arrays, ArrayResult{});
+    run_solve(s.get());
+    int status = MSTRESS_OK;
+    for (auto& r : s->results)
+        if (r.status != MSTRESS_OK) status = r.status;
+    *out = s.release();
+    if (status == MSTRESS_ENOT_CONVERGED) ctx->last_error = "PCG iteration limit reached";
+    if (status == MSTRESS_ENUMERIC) ctx->last_error = "PCG breakdown (non-positive curvature or NaN)";
+    return status;
+}
+
+}  // namespace
+}  // namespace ms
+
+mstress_sol_s::~mstress_sol_s() {
+    for (auto& g : graph)
+        if (g) cudaGraphExecDestroy(g);
+}
+
+using namespace ms;
+
+#define MS_API_BEGIN try {
+#define MS_API_END(ctx)                          \
+    }                                            \
+    catch (const ms::Error& e) {                 \
+        if (ctx) (ctx)->last_error = e.msg;      \
+        return e.code;                           \
+    }                                            \
+    catch (const std::exception& e) {            \
+        if (ctx) (ctx)->last_error = e.what();   \
+        return MSTRESS_EINVAL;                   \
+    }                                            \
+    return MSTRESS_OK;
+
+extern "C" {
+
+int mstress_solve(mstress_ctx ctx, const mstress_layout* layout, double dT, const mstress_bc* bc, mstress_sol* out) {
+    if (!ctx) return MSTRESS_EINVAL;
+    if (!out) { ctx->last_error = "out is NULL"; return MSTRESS_EINVAL; }
+    *out = nullptr;
+    MS_API_BEGIN
+    std::vector<LayoutIn> in{LayoutIn{layout, dT, bc}};
+    return solve_common(ctx, in, out);
+    MS_API_END(ctx)
+}
+
+int mstress_solve_batch(mstress_ctx ctx, const mstress_layout* layouts, const double* dT, const mstress_bc* bcs,
+                        int n, mstress_sol* out) {
+    if (!ctx) return MSTRESS_EINVAL;
+    if (!out) { ctx->last_error = "out is NULL"; return MSTRESS_EINVAL; }
+    *out = nullptr;
+    MS_API_BEGIN
+    MS_REQUIRE(layouts && dT && n >= 1, MSTRESS_EINVAL, "need n >= 1 layouts and dT values");
+    std::vector<LayoutIn> in;
+    for (int k = 0; k < n; ++k) in.push_back(LayoutIn{&layouts[k], dT[k], bcs ? &bcs[k] : nullptr});
+    return solve_common(ctx, in, out);
+    MS_API_END(ctx)
+}
+
+int mstress_sol_info(mstress_sol sol, int array, int* iters, int* outer, double* rel_res, int* status) {
+    if (!sol || array < 0 || array >= sol->n_arrays) return MSTRESS_EINVAL;
+    const ArrayResult& r = sol->results[array];
+    if (iters) *iters = r.iters;
+    if (outer) *outer = r.outer;
+    if (rel_res) *rel_res = r.rel_res;
+    if (status) *status = r.status;
+    return MSTRESS_OK;
+}
+
+int mstress_sol_count(mstress_sol sol, int* n_arrays, int64_t* n_blocks) {
+    if (!sol) return MSTRESS_EINVAL;
+    if (n_arrays) *n_arrays = sol->n_arrays;
+    if (n_blocks) *n_blocks = sol->n_blocks;
+    return MSTRESS_OK;
+}
+
+void mstress_free_sol(mstress_sol sol) {
+    if (!sol) return;
+    cudaStreamSynchronize(sol->ctx->stream);
+    delete sol;
+}
+
+int mstress_apply(mstress_ctx ctx, const mstress_layout* layout, const double* x_dev, double* y_dev, int precision) {
+    if (!ctx) return MSTRESS_EINVAL;
+    MS_API_BEGIN
+    MS_REQUIRE(x_dev && y_dev, MSTRESS_EINVAL, "x and y are required");
+    MS_REQUIRE(precision == MSTRESS_FP64, MSTRESS_EINVAL, "mstress_apply supports MSTRESS_FP64");
+    std::unique_ptr<mstress_sol_s> s(new mstress_sol_s());
+    s->ctx = ctx;
+    s->precision = MSTRESS_FP64;
+    mstress_bc bc{1, 0, nullptr, nullptr, 0};
+    std::vector<LayoutIn> in{LayoutIn{layout, 0.0, &bc}};
+    validate_and_build(s.get(), in);
+    launch_apply(s.get(), MSTRESS_FP64, x_dev, false, nullptr, s->Y.ptr);
+    launch_isum(s.get(), s->Y.ptr, false, x_dev, y_dev, false, nullptr, nullptr, nullptr);
+    MS_CUDA(cudaStreamSynchronize(ctx->stream));
+    MS_API_END(ctx)
+}
+
+int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, double* avg_ms) {
+    if (!ctx) return MSTRESS_EINVAL;
+    MS_API_BEGIN
+    MS_REQUIRE(sol && sol->ctx == ctx && avg_ms && reps >= 1, MSTRESS_EINVAL, "bad profile arguments");
+    mstress_sol_s* s = sol;
+    cudaStream_t st = ctx->stream;
+    const bool mixed = s->precision != MSTRESS_FP64;
+    DBuf y64, out;
+    if (phase == 2 && mixed) alloc_into(ctx, y64, (size_t)s->n_blocks * s->ldY * sizeof(double), false);
+    if (phase == 3) alloc_into(ctx, out, recover_bytes(s, MSTRESS_VM_ELEM), false);
+    auto run = [&]() {
+        switch (phase) {
+            case 0:
+                if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, true, nullptr, s->Y.ptr);
+                else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, false, nullptr, s->Y.ptr);
+                break;
+            case 1:
+                if (mixed) launch_isum(s, s->Y.ptr, true, s->v32.p.ptr, s->v32.q.ptr, true, s->dinv.as<double>(),
+                                       nullptr, s->part.as<double>());
+                else launch_isum(s, s->Y.ptr, false, s->v64.p.ptr, s->v64.q.ptr, false, s->dinv.as<double>(),
+                                 nullptr, s->part.as<double>());
+                break;
+            case 2:
+                launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, false, nullptr, mixed ? y64.ptr : s->Y.ptr);
+                break;
+            case 3:
+                recover(s, MSTRESS_VM_ELEM, out.ptr, true);
+                break;
+            default: throw Error{MSTRESS_EINVAL, "unknown phase"};
+        }
+    };
+    run();   // warm-up (and the one-time set-up of reduced-precision operands)
+    MS_CUDA(cudaStreamSynchronize(st));
+    cudaEvent_t e0, e1;
+    MS_CUDA(cudaEventCreate(&e0));
+    MS_CUDA(cudaEventCreate(&e1));
+    MS_CUDA(cudaEventRecord(e0, st));
+    for (int k = 0; k < reps; ++k) run();
+    MS_CUDA(cudaEventRecord(e1, st));
+    MS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    MS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *avg_ms = ms / reps;
+    MS_API_END(ctx)
+}
+
+int mstress_recover_size(mstress_sol sol, int what, size_t* bytes) {
+    if (!sol || !bytes) return MSTRESS_EINVAL;
+    MS_API_BEGIN
+    *bytes = recover_bytes(sol, what);
+    MS_API_END(sol->ctx)
+}
+
+int mstress_recover(mstress_ctx ctx, mstress_sol sol, int what, void* dst, size_t dst_bytes, int dst_on_device) {
+    if (!ctx) return MSTRESS_EINVAL;
+    MS_API_BEGIN
+    MS_REQUIRE(sol && sol->ctx == ctx, MSTRESS_EINVAL, "solution is NULL or from another context");
+    MS_REQUIRE(dst, MSTRESS_EINVAL, "dst is NULL");
+    size_t need = recover_bytes(sol, what);
+    MS_REQUIRE(dst_bytes >= need, MSTRESS_EINVAL, "dst too small: need " + std::to_string(need) + " B");
+    recover(sol, what, dst, dst_on_device != 0);
+    MS_API_END(ctx)
+}
+
+}  // extern "C"
