@@ -129,7 +129,7 @@ typedef struct {
 } mstress_opts;
 
 /* Fill *o with defaults: FP64, rtol 1e-13, max_iter 20000, inner_rtol 1e-4,
-   max_outer 12, hbm_budget 0, offline_max_iter 20000, offline_rtol 1e-13. */
+   max_outer 30, hbm_budget 0, offline_max_iter 20000, offline_rtol 1e-13. */
 int mstress_opts_default(mstress_opts* o);
 
 /* ------------------------------------------------------------ context */

@@ -121,7 +121,7 @@ int mstress_opts_default(mstress_opts* o) {
     o->rtol = 1e-13;
     o->max_iter = 20000;
     o->inner_rtol = 1e-4;
-    o->max_outer = 12;
+    o->max_outer = 30;
     o->hbm_budget = 0;
     o->offline_max_iter = 20000;
     o->offline_rtol = 1e-13;

@@ -67,3 +67,5 @@ def test_refinement_reaches_fp64_accuracy(blocks_fp64, mode):
     assert info["status"] == 0 and info["rel_res"] <= 1e-12
     assert rel_l2(c, osol.coeffs) <= 1e-9
     assert np.all(err <= bound + 1e-12 * ovm.max())
+    if mode == L.MSTRESS_BF16X3:      # the mixed-path accuracy target for von Mises
+        assert rel_l2(vm, ovm) <= 1e-4
