@@ -97,7 +97,7 @@ struct VecWork { int array, pad; long long start, count; };  // packed lattice D
 
 struct PcgState {            // per-array conjugate-gradient scalars
     double rz, rr, bb, tol2;
-    double res0;             // ||b||^2 of the outer problem (mixed modes)
+    double beta;             // pending p = z + beta p of the next iteration
     int iters, active, status, max_iter;
 };
 
@@ -139,6 +139,8 @@ struct mstress_block_s {
     ms::DBuf Kr, br, S, Smean, F;
     // lazily created low-precision operand copies, by precision mode
     ms::DBuf Kr_lp[4], Smean_lp[4], S_lp[4];
+    // tensor-core operand images (K-major, no-swizzle core-matrix layout), by precision mode
+    ms::DBuf Kr_tc[4], Smean_tc[4];
 };
 
 namespace ms {

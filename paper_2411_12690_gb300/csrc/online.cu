@@ -3,23 +3,28 @@
 // The reduced global system A_global u = b_global is never assembled. Blocks
 // act as abstract elements (section 4.3): block (i, j) of an nx*ny array owns
 // the Lagrange-lattice points (i(n-1)+a, j(n-1)+b, c) of its surface nodes
-// (a, b, c), so the element-to-global map is arithmetic. One PCG iteration is
-//   1. apply:   Y_e = A_element[type e] * p[G_e]   for every block e   (Eq. 18)
-//   2. isum:    q_g = sum of Y_e over the <= 4 blocks owning lattice DOF g,
-//               in a fixed order (bitwise reproducible), and <p, q> partials
-//   3. vec1:    alpha, x += alpha p, r -= alpha q, z = D^-1 r, <r,z>, <r,r> partials
-//   4. vec2:    beta, p = z + beta p
-//   5. scalars: per-array reductions, stopping test, iteration count
-// Every phase is one launch over the work items of all arrays of a batch
-// (a grid-stride "persistent" loop), each array with its own scalars. The
-// iteration is captured once as a CUDA graph and replayed. Constrained DOFs
-// (clamped faces, prescribed values) have D^-1 = 0, which keeps r, z, p zero
-// there; prescribed values enter b by lifting (Eq. 13).
+// (a, b, c), so the element-to-global map is arithmetic. One Jacobi-PCG
+// iteration is three launches:
+//   1. apply:  gather p_e = G_e p for every block (with the pending update
+//              p = z + beta p folded into the gather) and form the element
+//              products Y_e = A_element[type e] p_e                    (Eq. 18)
+//   2. isum:   q_g = sum of Y_e over the <= 4 blocks owning lattice DOF g, in
+//              a fixed order (bitwise reproducible); stores the updated p and
+//              the <p, q> partial sums
+//   3. vec1:   alpha = <r,z>/<p,q>, x += alpha p, r -= alpha q, z = D^-1 r and
+//              the <r,z>, <r,r> partials; the last CTA to finish folds them per
+//              array (beta, stopping test, iteration count) and sets the
+//              loop condition of the CUDA graph.
+// Every phase is one launch over the work items of all arrays of a batch (a
+// grid-stride persistent loop), each array with its own scalars. The loop runs
+// as a CUDA-graph conditional WHILE node: one graph launch per solve, no host
+// polling. Constrained DOFs (clamped faces, prescribed values) have D^-1 = 0,
+// which keeps r, z, p zero there; prescribed values enter b by lifting (Eq. 13).
 //
 // Precision: FP64 vectors and FP64 operator in the plain mode; in the mixed
-// modes an FP64 outer loop (residual b - A x with the FP64 operator) drives an
-// inner PCG with FP32 vectors and a reduced-precision operator, while all dot
-// products and step lengths stay FP64.
+// modes an FP64 outer loop (residual b - A x with the FP64 operator, a5)
+// drives an inner PCG with FP32 vectors and a reduced-precision operator, while
+// all dot products and step lengths stay FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -34,11 +39,20 @@ constexpr int kThreads = 256;
 
 // ----------------------------------------------------------- reductions
 // Fixed-order sum of n values by one warp: lane-strided partial sums, then a
-// butterfly. Every caller that folds the same array gets the same bits.
+// butterfly. Every caller that folds the same array gets the same bits. Loads
+// bypass L1 because the values come from other CTAs.
 __device__ __forceinline__ double warp_fold(const double* v, int n) {
     const int lane = threadIdx.x & 31;
     double s = 0;
-    for (int i = lane; i < n; i += 32) s += v[i];
+    int i = lane;
+    for (; i + 96 < n; i += 128) {   // four loads in flight, summed in index order
+        const double a0 = __ldcg(v + i), a1 = __ldcg(v + i + 32), a2 = __ldcg(v + i + 64), a3 = __ldcg(v + i + 96);
+        s += a0;
+        s += a1;
+        s += a2;
+        s += a3;
+    }
+    for (; i < n; i += 32) s += __ldcg(v + i);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
@@ -57,13 +71,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 __device__ __forceinline__ void lattice_coords(const ArrayDev& A, long long g, int& comp, int& gx, int& gy,
                                                int& gz) {
-    long long l = g - A.vec_off;
-    long long node = l / 3;
-    comp = (int)(l - 3 * node);
-    gx = (int)(node % A.X);
-    long long t = node / A.X;
-    gy = (int)(t % A.Y);
-    gz = (int)(t / A.Y);
+    // an array's lattice holds fewer than 2^31 DOFs, so 32-bit division suffices
+    const unsigned l = (unsigned)(g - A.vec_off);
+    const unsigned node = l / 3u;
+    comp = (int)(l - 3u * node);
+    const unsigned X = (unsigned)A.X, t = node / X;
+    gx = (int)(node - t * X);
+    const unsigned Y = (unsigned)A.Y, zz = t / Y;
+    gy = (int)(t - zz * Y);
+    gz = (int)zz;
 }
 
 // Visit the blocks that own lattice point (gx, gy, gz) with the point's
@@ -125,91 +141,72 @@ __global__ void __launch_bounds__(kThreads) k_rhs_diag(const __grid_constant__ R
 }
 
 // ------------------------------------------------------ a3: operator apply
-struct ApplyArgs {
-    const ApplyWork* work;
-    int n_work;
-    const int* blist;
-    const BlockRef* bref;
-    const ArrayDev* arrays;
-    const LocalMap* lm;
-    const PcgState* st;    // optional: skip arrays that stopped
-    TypeTab tt;
-    int m, ldY;
-    const void* x;
-    void* Y;
-};
-
-// Shared part of the gather: per-tile lattice base of each block and the
-// per-array offset of each element DOF.
-__device__ __forceinline__ void tile_setup(const ApplyArgs& a, const ApplyWork& it, const ArrayDev& A, long long* base,
-                                           int* offs) {
-    const int n1 = a.lm->n - 1;
-    for (int k = threadIdx.x; k < a.m; k += kThreads) {
-        int q = k / 3, c = k - 3 * q;
-        offs[k] = ((a.lm->qc[q] * A.Y + a.lm->qb[q]) * A.X + a.lm->qa[q]) * 3 + c;
-    }
-    if (threadIdx.x < kTile64 && threadIdx.x < it.count) {
-        BlockRef br = a.bref[a.blist[it.start + threadIdx.x]];
-        base[threadIdx.x] = A.vec_off + 3LL * ((long long)br.j * n1 * A.X + (long long)br.i * n1);
-    }
-}
-
-// FP64 element products, tiles of 32 blocks of one type and one array.
-// Shared: C [m][32] (gathered coefficients), K panel [8*RPT][m].
+// FP64 element products. A work item is one panel of 8*RPT rows of A_element
+// for a tile of 32 blocks of one type and one array, so that the items (and
+// the FP64 work) spread evenly over the SMs. Shared: C [m][32] (gathered
+// coefficients), K panel [8*RPT][m].
 template <int RPT>
 __global__ void __launch_bounds__(kThreads) k_apply64(const __grid_constant__ ApplyArgs a) {
     extern __shared__ double sm[];
     __shared__ long long base[kTile64];
     __shared__ int offs[3 * kMaxSurf];
     const int m = a.m;
+    const int n_panels = (m + 8 * RPT - 1) / (8 * RPT);
     double* Cs = sm;
     double* Ks = sm + (size_t)m * kTile64;
     const double* __restrict__ x = static_cast<const double*>(a.x);
+    const double* __restrict__ z = static_cast<const double*>(a.z);
     double* __restrict__ Y = static_cast<double*>(a.Y);
-    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
-        const ApplyWork it = a.work[w];
+    for (int w = blockIdx.x; w < a.n_work * n_panels; w += gridDim.x) {
+        const ApplyWork it = a.work[w / n_panels];
+        const int panel = w % n_panels;
         if (a.st && !a.st[it.array].active) continue;
         const ArrayDev A = a.arrays[it.array];
+        const double beta = a.st ? a.st[it.array].beta : 0.0;
         __syncthreads();
-        tile_setup(a, it, A, base, offs);
+        tile_setup(a, it, A, base, offs, kTile64);
         __syncthreads();
         for (int idx = threadIdx.x; idx < m * kTile64; idx += kThreads) {
             int k = idx >> 5, bt = idx & 31;
-            Cs[idx] = bt < it.count ? x[base[bt] + offs[k]] : 0.0;
+            double v = 0.0;
+            if (bt < it.count) {
+                long long g = base[bt] + offs[k];
+                v = z ? p_next(z[g], x[g], beta) : x[g];
+            }
+            Cs[idx] = v;
         }
         const double* __restrict__ K = a.tt.Kr[it.type];
         const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
-        for (int r0 = 0; r0 < m; r0 += 8 * RPT) {
-            __syncthreads();
-            const int rows = min(8 * RPT, m - r0);
-            for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += kThreads)
-                Ks[idx] = idx < rows * m ? K[(size_t)r0 * m + idx] : 0.0;
-            __syncthreads();
-            double acc[RPT];
+        const int r0 = panel * 8 * RPT;
+        const int rows = min(8 * RPT, m - r0);
+        for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += kThreads)
+            Ks[idx] = idx < rows * m ? K[(size_t)r0 * m + idx] : 0.0;
+        __syncthreads();
+        double acc[RPT];
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) acc[u] = 0;
-            const double* kr = Ks + rg * RPT * m;
-            for (int k = 0; k < m; ++k) {
-                double c = Cs[k * kTile64 + bt];
+        for (int u = 0; u < RPT; ++u) acc[u] = 0;
+        const double* kr = Ks + rg * RPT * m;
+        for (int k = 0; k < m; ++k) {
+            double c = Cs[k * kTile64 + bt];
 #pragma unroll
-                for (int u = 0; u < RPT; ++u) acc[u] = fma(kr[u * m + k], c, acc[u]);
-            }
-            if (bt < it.count) {
-                const long long e = a.blist[it.start + bt];
+            for (int u = 0; u < RPT; ++u) acc[u] = fma(kr[u * m + k], c, acc[u]);
+        }
+        if (bt < it.count) {
+            const long long e = a.blist[it.start + bt];
 #pragma unroll
-                for (int u = 0; u < RPT; ++u) {
-                    int r = r0 + rg * RPT + u;
-                    if (r < m) Y[e * a.ldY + r] = acc[u];
-                }
+            for (int u = 0; u < RPT; ++u) {
+                int r = r0 + rg * RPT + u;
+                if (r < m) Y[e * a.ldY + r] = acc[u];
             }
         }
     }
 }
 
-// Reduced-precision element products on CUDA cores (FP32 vectors). The
-// operator copy Klp holds K rounded to the mode's operand format (stored as
-// float); BF16X3 holds [K_hi; K_lo]. The gathered coefficients are rounded the
-// same way and products accumulate in FP32, as on the tensor cores.
+// Reduced-precision element products on CUDA cores (FP32 vectors), used when
+// the tensor-core path does not cover the basis size. The operator copy Klp
+// holds K rounded to the mode's operand format (stored as float); BF16X3 holds
+// [K_hi; K_lo]. The gathered coefficients are rounded the same way and the
+// products accumulate in FP32, as on the tensor cores.
 __device__ __forceinline__ float round_tf32(float v) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
@@ -227,17 +224,23 @@ __global__ void __launch_bounds__(kThreads) k_apply32(const __grid_constant__ Ap
     float* Cs = smf;                                   // [NS][m][32]
     float* Ks = smf + (size_t)NS * m * kTile64;        // [NS][8*RPT][m]
     const float* __restrict__ x = static_cast<const float*>(a.x);
+    const float* __restrict__ z = static_cast<const float*>(a.z);
     float* __restrict__ Y = static_cast<float*>(a.Y);
     for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
         const ApplyWork it = a.work[w];
         if (a.st && !a.st[it.array].active) continue;
         const ArrayDev A = a.arrays[it.array];
+        const double beta = a.st ? a.st[it.array].beta : 0.0;
         __syncthreads();
-        tile_setup(a, it, A, base, offs);
+        tile_setup(a, it, A, base, offs, kTile64);
         __syncthreads();
         for (int idx = threadIdx.x; idx < m * kTile64; idx += kThreads) {
             int k = idx >> 5, bt = idx & 31;
-            float v = bt < it.count ? x[base[bt] + offs[k]] : 0.0f;
+            float v = 0.0f;
+            if (bt < it.count) {
+                long long g = base[bt] + offs[k];
+                v = z ? p_next(z[g], x[g], beta) : x[g];
+            }
             if (MODE == MSTRESS_TF32) Cs[idx] = round_tf32(v);
             else if (MODE == MSTRESS_BF16) Cs[idx] = round_bf16(v);
             else {
@@ -289,11 +292,12 @@ struct IsumArgs {
     int n_vwork;
     const ArrayDev* arrays;
     const LocalMap* lm;
-    const PcgState* st;     // optional: skip stopped arrays
+    const PcgState* st;     // optional: skip stopped arrays, beta of the p update
     const double* dinv;     // optional: zero the constrained rows
     int ldY;
     const void* Y;
-    const void* p;
+    void* p;                // direction (updated in place when z is given)
+    const void* z;          // optional: p = z + beta p before use
     void* q;
     double* part_pq;        // optional
 };
@@ -303,12 +307,14 @@ template <class V, class YT>
 __global__ void __launch_bounds__(kThreads) k_isum(const __grid_constant__ IsumArgs a) {
     __shared__ double sh[kThreads / 32];
     const YT* __restrict__ Y = static_cast<const YT*>(a.Y);
-    const V* __restrict__ p = static_cast<const V*>(a.p);
+    V* __restrict__ p = static_cast<V*>(a.p);
+    const V* __restrict__ z = static_cast<const V*>(a.z);
     V* __restrict__ q = static_cast<V*>(a.q);
     for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
         const VecWork it = a.vwork[w];
         if (a.st && !a.st[it.array].active) continue;
         const ArrayDev A = a.arrays[it.array];
+        const double beta = a.st ? a.st[it.array].beta : 0.0;
         double acc = 0;
         for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
             double s = 0;
@@ -319,8 +325,13 @@ __global__ void __launch_bounds__(kThreads) k_isum(const __grid_constant__ IsumA
                     s += (double)Y[blk * a.ldY + 3 * sidx + comp];
                 });
             }
+            V pv = p[g];
+            if (z) {
+                pv = p_next(z[g], pv, beta);
+                p[g] = pv;
+            }
             q[g] = (V)s;
-            acc += (double)p[g] * s;
+            acc += (double)pv * s;
         }
         if (a.part_pq) {
             double t = block_sum(acc, sh);
@@ -334,13 +345,20 @@ struct VecArgs {
     const VecWork* vwork;
     int n_vwork;
     const ArrayDev* arrays;
+    int n_arrays;
     PcgState* st;
     const double* dinv;
     void *x, *r, *z, *p, *q;
-    const void* rhs;        // init: right-hand side (FP64)
+    const void* rhs;        // init / residual: right-hand side (FP64)
     double *part_pq, *part_rz, *part_rr;
+    int* flag;              // [0] any active, [1] CTA ticket, [2] device error, [3] loop count
+    int loop_cap;           // hard cap on loop iterations of the graph WHILE node
+    int use_cond;
+    cudaGraphConditionalHandle cond;
 };
 
+// x = 0, r = rhs on free DOFs, z = D^-1 r, p = 0 (so the first fused update
+// gives p = z); partials <r,z>, <r,r>.
 template <class V>
 __global__ void __launch_bounds__(kThreads) k_pcg_init(const __grid_constant__ VecArgs a) {
     __shared__ double sh[kThreads / 32];
@@ -356,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(const __grid_constant__ V
             x[g] = (V)0;
             r[g] = rv;
             z[g] = zv;
-            p[g] = zv;
+            p[g] = (V)0;
             srz += (double)rv * (double)zv;
             srr += (double)rv * (double)rv;
         }
@@ -366,10 +384,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(const __grid_constant__ V
     }
 }
 
+// alpha, x += alpha p, r -= alpha q, z = D^-1 r, partials; then the last CTA
+// folds the partials of every active array: beta = <r,z>_new / <r,z>_old,
+// stopping test on <r,r>, iteration count, and the graph loop condition.
 template <class V>
 __global__ void __launch_bounds__(kThreads) k_vec1(const __grid_constant__ VecArgs a) {
     __shared__ double sh[kThreads / 32];
     __shared__ double s_alpha;
+    __shared__ int s_last;
     V *x = (V*)a.x, *r = (V*)a.r, *z = (V*)a.z;
     const V *p = (const V*)a.p, *q = (const V*)a.q;
     for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
@@ -400,27 +422,46 @@ __global__ void __launch_bounds__(kThreads) k_vec1(const __grid_constant__ VecAr
         srr = block_sum(srr, sh);
         if (threadIdx.x == 0) { a.part_rz[w] = srz; a.part_rr[w] = srr; }
     }
-}
-
-template <class V>
-__global__ void __launch_bounds__(kThreads) k_vec2(const __grid_constant__ VecArgs a) {
-    __shared__ double s_beta;
-    const V* z = (const V*)a.z;
-    V* p = (V*)a.p;
-    for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
-        const VecWork it = a.vwork[w];
-        const PcgState st = a.st[it.array];
-        if (!st.active) continue;
-        const ArrayDev A = a.arrays[it.array];
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
-            if (threadIdx.x == 0) s_beta = rz / st.rz;
+    // ---- last CTA: per-array scalar phase
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.flag[1], 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int any = 0;
+    for (int k = warp; k < a.n_arrays; k += kThreads / 32) {
+        PcgState s = a.st[k];
+        if (!s.active) continue;
+        const ArrayDev A = a.arrays[k];
+        double pq = warp_fold(a.part_pq + A.vwork_off, A.n_vwork);
+        double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
+        double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
+        if (lane == 0) {
+            s.iters += 1;
+            if (!(pq > 0) || !isfinite(rz) || !isfinite(rr)) {
+                s.active = 0;
+                s.status = MSTRESS_ENUMERIC;
+            } else {
+                s.beta = rz / s.rz;
+                s.rz = rz;
+                s.rr = rr;
+                if (rr <= s.tol2) { s.active = 0; s.status = MSTRESS_OK; }
+                else if (s.iters >= s.max_iter) { s.active = 0; s.status = MSTRESS_ENOT_CONVERGED; }
+            }
+            a.st[k] = s;
+            any |= s.active;
         }
-        __syncthreads();
-        const double be = s_beta;
-        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads)
-            p[g] = (V)((double)z[g] + be * (double)p[g]);
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        a.flag[1] = 0;
+        int loops = a.flag[3] + 1;
+        a.flag[3] = loops;
+        if (loops >= a.loop_cap) any = 0;
+        a.flag[0] = any;
+        if (a.use_cond) cudaGraphSetConditional(a.cond, any ? 1u : 0u);
     }
 }
 
@@ -465,16 +506,19 @@ __global__ void k_lift_rhs(long long n, double* b, const double* Axbc, const dou
 }
 
 // ----------------------------------------------------- a4: scalar phase
+// mode 1: start of a PCG run (tolerance from rtol, beta = 0, gate: only arrays
+// active in `gate` start); mode 2: outer refinement check (part_rr holds
+// ||b - A x||^2 partials, st.bb = ||b||^2, iters counts refinement steps).
 struct ScalarArgs {
     int n_arrays;
     const ArrayDev* arrays;
     PcgState* st;
-    const double *part_pq, *part_rz, *part_rr;
-    int* any;
-    int mode;         // 0: iteration, 1: PCG start (tol from rtol), 2: outer residual check
+    const double *part_rz, *part_rr;
+    int* flag;
+    int mode;
     double rtol;
     int max_iter;
-    const PcgState* gate;   // mode 1: only arrays active here start (may be NULL)
+    const PcgState* gate;
 };
 
 __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ ScalarArgs a) {
@@ -483,25 +527,7 @@ __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ Scalar
     for (int k = warp; k < a.n_arrays; k += 32) {
         const ArrayDev A = a.arrays[k];
         PcgState s = a.st[k];
-        if (a.mode == 0) {
-            if (!s.active) continue;
-            double pq = warp_fold(a.part_pq + A.vwork_off, A.n_vwork);
-            double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
-            double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
-            if (lane == 0) {
-                s.iters += 1;
-                if (!(pq > 0) || !isfinite(rz) || !isfinite(rr)) {
-                    s.active = 0;
-                    s.status = MSTRESS_ENUMERIC;
-                } else {
-                    s.rz = rz;
-                    s.rr = rr;
-                    if (rr <= s.tol2) { s.active = 0; s.status = MSTRESS_OK; }
-                    else if (s.iters >= s.max_iter) { s.active = 0; s.status = MSTRESS_ENOT_CONVERGED; }
-                }
-                a.st[k] = s;
-            }
-        } else if (a.mode == 1) {
+        if (a.mode == 1) {
             double rz = warp_fold(a.part_rz + A.vwork_off, A.n_vwork);
             double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
             if (lane == 0) {
@@ -510,14 +536,14 @@ __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ Scalar
                 s.rr = rr;
                 s.bb = rr;
                 s.tol2 = a.rtol * a.rtol * rr;
+                s.beta = 0.0;
                 s.iters = 0;
                 s.max_iter = a.max_iter;
-                s.status = MSTRESS_OK;
+                s.status = isfinite(rr) ? MSTRESS_OK : MSTRESS_ENUMERIC;
                 s.active = (gate && rr > 0 && isfinite(rr)) ? 1 : 0;
-                if (!isfinite(rr)) s.status = MSTRESS_ENUMERIC;
                 a.st[k] = s;
             }
-        } else {   // outer check: part_rr holds ||b - A x||^2 partials; s.bb = ||b||^2
+        } else {
             double rr = warp_fold(a.part_rr + A.vwork_off, A.n_vwork);
             if (lane == 0) {
                 s.rr = rr;
@@ -533,29 +559,16 @@ __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ Scalar
         if (lane == 0) any |= a.st[k].active;
     }
     any = __syncthreads_or(any);
-    if (threadIdx.x == 0 && a.any) *a.any = any;
+    if (threadIdx.x == 0) {
+        a.flag[0] = any;
+        a.flag[1] = 0;
+        a.flag[3] = 0;
+    }
 }
 
 // ------------------------------------------------------------ launches
 int grid_for(mstress_sol_s* s, int items, int per_sm) {
     return std::max(1, std::min(items, s->ctx->num_sms * per_sm));
-}
-
-ApplyArgs apply_args(mstress_sol_s* s, const void* x, const PcgState* st, void* Y) {
-    ApplyArgs a;
-    a.work = s->d_awork.as<ApplyWork>();
-    a.n_work = s->n_awork;
-    a.blist = s->d_blist.as<int>();
-    a.bref = s->d_bref.as<BlockRef>();
-    a.arrays = s->d_arrays.as<ArrayDev>();
-    a.lm = s->d_lm.as<LocalMap>();
-    a.st = st;
-    a.tt = s->tt;
-    a.m = s->m;
-    a.ldY = s->ldY;
-    a.x = x;
-    a.Y = Y;
-    return a;
 }
 
 constexpr int kMaxDynSmem = 200 * 1024;
@@ -566,7 +579,7 @@ void configure_apply_kernels(int device) {
     static bool done[64] = {};
     if (device < 0 || device >= 64 || done[device]) return;
     auto set = [](auto k) { MS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)); };
-    set(k_apply64<10>);
+    set(k_apply64<2>);
     set(k_apply64<4>);
     set(k_apply32<10, MSTRESS_TF32>);
     set(k_apply32<10, MSTRESS_BF16>);
@@ -574,22 +587,25 @@ void configure_apply_kernels(int device) {
     set(k_apply32<4, MSTRESS_TF32>);
     set(k_apply32<4, MSTRESS_BF16>);
     set(k_apply32<4, MSTRESS_BF16X3>);
+    configure_tc_kernels();
     done[device] = true;
 }
 
 template <class KER>
-void launch_with_smem(KER kernel, mstress_sol_s* s, size_t smem, const ApplyArgs& a) {
+void launch_with_smem(KER kernel, mstress_sol_s* s, size_t smem, const ApplyArgs& a, int items_per_work = 1) {
     MS_REQUIRE(smem <= (size_t)kMaxDynSmem, MSTRESS_EINVAL, "apply tile does not fit in shared memory");
-    int per_sm = smem > 110 * 1024 ? 1 : (smem > 70 * 1024 ? 2 : 3);
-    kernel<<<grid_for(s, a.n_work, per_sm), kThreads, smem, s->ctx->stream>>>(a);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / (smem + 4096)));
+    kernel<<<grid_for(s, a.n_work * items_per_work, per_sm), kThreads, smem, s->ctx->stream>>>(a);
     MS_LAUNCH_CHECK();
 }
 
 VecArgs vec_args(mstress_sol_s* s, PcgVectors& v) {
     VecArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.vwork = s->d_vwork.as<VecWork>();
     a.n_vwork = s->n_vwork;
     a.arrays = s->d_arrays.as<ArrayDev>();
+    a.n_arrays = s->n_arrays;
     a.st = v.state.as<PcgState>();
     a.dinv = s->dinv.as<double>();
     a.x = v.x.ptr;
@@ -597,10 +613,11 @@ VecArgs vec_args(mstress_sol_s* s, PcgVectors& v) {
     a.z = v.z.ptr;
     a.p = v.p.ptr;
     a.q = v.q.ptr;
-    a.rhs = nullptr;
     a.part_pq = s->part.as<double>();
     a.part_rz = a.part_pq + s->n_vwork;
     a.part_rr = a.part_rz + s->n_vwork;
+    a.flag = s->flag.as<int>();
+    a.loop_cap = 1 << 30;
     return a;
 }
 
@@ -609,10 +626,9 @@ ScalarArgs scalar_args(mstress_sol_s* s, PcgVectors& v, int mode, double rtol, i
     a.n_arrays = s->n_arrays;
     a.arrays = s->d_arrays.as<ArrayDev>();
     a.st = v.state.as<PcgState>();
-    a.part_pq = s->part.as<double>();
-    a.part_rz = a.part_pq + s->n_vwork;
+    a.part_rz = s->part.as<double>() + s->n_vwork;
     a.part_rr = a.part_rz + s->n_vwork;
-    a.any = s->flag.as<int>();
+    a.flag = s->flag.as<int>();
     a.mode = mode;
     a.rtol = rtol;
     a.max_iter = max_iter;
@@ -622,16 +638,44 @@ ScalarArgs scalar_args(mstress_sol_s* s, PcgVectors& v, int mode, double rtol, i
 
 }  // namespace
 
-void launch_apply(mstress_sol_s* s, int prec, const void* x, bool vec_fp32, const PcgState* st, void* Y) {
-    ApplyArgs a = apply_args(s, x, st, Y);
+ApplyArgs apply_args(mstress_sol_s* s, const void* x, const void* z, const PcgState* st, void* Y, bool tc) {
+    ApplyArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.work = tc ? s->d_awork_tc.as<ApplyWork>() : s->d_awork.as<ApplyWork>();
+    a.n_work = tc ? s->n_awork_tc : s->n_awork;
+    a.blist = s->d_blist.as<int>();
+    a.bref = s->d_bref.as<BlockRef>();
+    a.arrays = s->d_arrays.as<ArrayDev>();
+    a.lm = s->d_lm.as<LocalMap>();
+    a.st = st;
+    a.tt = s->tt;
+    a.m = s->m;
+    a.ldY = s->ldY;
+    a.x = x;
+    a.z = z;
+    a.Y = Y;
+    a.err = s->flag.as<int>() + 2;
+    return a;
+}
+
+void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool vec_fp32, const PcgState* st,
+                  void* Y) {
     const int m = s->m;
     if (prec == MSTRESS_FP64) {
         MS_REQUIRE(!vec_fp32, MSTRESS_EINVAL, "FP64 apply needs FP64 vectors");
-        if (m <= 80) launch_with_smem(k_apply64<10>, s, (size_t)(m * kTile64 + 80 * m) * sizeof(double), a);
-        else launch_with_smem(k_apply64<4>, s, (size_t)(m * kTile64 + 32 * m) * sizeof(double), a);
+        ApplyArgs a = apply_args(s, x, z, st, Y, false);
+        if (m <= 80)
+            launch_with_smem(k_apply64<2>, s, (size_t)(m * kTile64 + 16 * m) * sizeof(double), a, (m + 15) / 16);
+        else
+            launch_with_smem(k_apply64<4>, s, (size_t)(m * kTile64 + 32 * m) * sizeof(double), a, (m + 31) / 32);
         return;
     }
     MS_REQUIRE(vec_fp32, MSTRESS_EINVAL, "reduced-precision apply needs FP32 vectors");
+    if (s->use_tc) {
+        launch_apply_tc(s, prec, apply_args(s, x, z, st, Y, true));
+        return;
+    }
+    ApplyArgs a = apply_args(s, x, z, st, Y, false);
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
     if (m <= 80) {
         size_t smem = (size_t)ns * (m * kTile64 + 80 * m) * sizeof(float);
@@ -646,7 +690,7 @@ void launch_apply(mstress_sol_s* s, int prec, const void* x, bool vec_fp32, cons
     }
 }
 
-void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, const void* p, void* q, bool vec_fp32,
+void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, void* p, const void* z, void* q, bool vec_fp32,
                  const double* dinv, const PcgState* st, double* part_pq) {
     IsumArgs a;
     a.vwork = s->d_vwork.as<VecWork>();
@@ -658,40 +702,38 @@ void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, const void* p, vo
     a.ldY = s->ldY;
     a.Y = Y;
     a.p = p;
+    a.z = z;
     a.q = q;
     a.part_pq = part_pq;
     int g = grid_for(s, s->n_vwork, 8);
     cudaStream_t stream = s->ctx->stream;
     if (!vec_fp32 && !y_fp32) k_isum<double, double><<<g, kThreads, 0, stream>>>(a);
     else if (vec_fp32 && y_fp32) k_isum<float, float><<<g, kThreads, 0, stream>>>(a);
-    else if (!vec_fp32 && y_fp32) k_isum<double, float><<<g, kThreads, 0, stream>>>(a);
     else MS_REQUIRE(false, MSTRESS_EINVAL, "unsupported isum types");
     MS_LAUNCH_CHECK();
 }
 
 namespace {
 
-// One PCG iteration over all arrays (five launches), on vectors v of type V.
+// One PCG iteration over all arrays: apply, interface sum, vector update.
 template <class V>
-void pcg_iteration(mstress_sol_s* s, PcgVectors& v, int prec) {
+void pcg_iteration(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond, cudaGraphConditionalHandle cond,
+                   int loop_cap) {
     constexpr bool f32 = std::is_same<V, float>::value;
     cudaStream_t stream = s->ctx->stream;
     const PcgState* st = v.state.as<PcgState>();
-    launch_apply(s, prec, v.p.ptr, f32, st, s->Y.ptr);
-    launch_isum(s, s->Y.ptr, f32, v.p.ptr, v.q.ptr, f32, s->dinv.as<double>(), st, s->part.as<double>());
+    launch_apply(s, prec, v.p.ptr, v.z.ptr, f32, st, s->Y.ptr);
+    launch_isum(s, s->Y.ptr, f32, v.p.ptr, v.z.ptr, v.q.ptr, f32, s->dinv.as<double>(), st, s->part.as<double>());
     VecArgs va = vec_args(s, v);
-    int g = grid_for(s, s->n_vwork, 8);
-    k_vec1<V><<<g, kThreads, 0, stream>>>(va);
-    MS_LAUNCH_CHECK();
-    k_vec2<V><<<g, kThreads, 0, stream>>>(va);
-    MS_LAUNCH_CHECK();
-    ScalarArgs sa = scalar_args(s, v, 0, 0, 0, nullptr);
-    k_scalars<<<1, 1024, 0, stream>>>(sa);
+    va.use_cond = use_cond;
+    va.cond = cond;
+    va.loop_cap = loop_cap;
+    k_vec1<V><<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
     MS_LAUNCH_CHECK();
 }
 
 // Start a PCG run on right-hand side rhs (FP64 device vector): x = 0, r = rhs
-// on free DOFs, z = D^-1 r, p = z; tolerance rtol relative to ||rhs||.
+// on free DOFs, z = D^-1 r, p = 0, beta = 0; tolerance rtol relative to ||rhs||.
 template <class V>
 void pcg_start(mstress_sol_s* s, PcgVectors& v, const double* rhs, double rtol, int max_iter, const PcgState* gate) {
     cudaStream_t stream = s->ctx->stream;
@@ -704,62 +746,84 @@ void pcg_start(mstress_sol_s* s, PcgVectors& v, const double* rhs, double rtol, 
     MS_LAUNCH_CHECK();
 }
 
-constexpr int kGraphIters = 16;
+constexpr int kChunkIters = 16;
 
-// Iterate until every array has stopped: replay a captured graph of
-// kGraphIters iterations, polling the device any-active flag between replays.
+// Build the solve's graph: one conditional WHILE node whose body is one PCG
+// iteration; the last CTA of the vector phase clears the condition when no
+// array is still iterating (or the loop cap is reached).
+template <class V>
+bool build_while_graph(mstress_sol_s* s, PcgVectors& v, int prec, int gi, int max_iter) {
+    cudaStream_t stream = s->ctx->stream;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    cudaGraphConditionalHandle h;
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cudaGraphNode_t node;
+    bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            g_capturing = true;
+            try {
+                pcg_iteration<V>(s, v, prec, 1, h, max_iter + 2);
+            } catch (...) {
+                ok = false;
+            }
+            g_capturing = false;
+            cudaGraph_t out = nullptr;
+            ok = (cudaStreamEndCapture(stream, &out) == cudaSuccess) && ok;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&s->graph[gi], g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (!ok) s->graph[gi] = nullptr;
+    s->graph_iters[gi] = 3;   // kernel nodes per loop iteration
+    return ok;
+}
+
+// Iterate until every array has stopped.
 template <class V>
 void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
     constexpr int gi = std::is_same<V, float>::value ? 1 : 0;
     cudaStream_t stream = s->ctx->stream;
-    if (stream == nullptr) {   // the legacy default stream cannot be captured: launch directly
-        for (int done_iters = 0; done_iters < max_iter; done_iters += kGraphIters) {
-            for (int k = 0; k < kGraphIters; ++k) pcg_iteration<V>(s, v, prec);
-            MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
-            MS_CUDA(cudaStreamSynchronize(stream));
-            if (s->ctx->h_flag[0] == 0) break;
-        }
+    int* flag = s->flag.as<int>();
+    if (stream != nullptr && !s->graph[gi] && !s->no_while[gi]) s->no_while[gi] = !build_while_graph<V>(s, v, prec, gi, max_iter);
+    if (s->graph[gi]) {
+        MS_CUDA(cudaGraphLaunch(s->graph[gi], stream));
+        MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
+        MS_CUDA(cudaStreamSynchronize(stream));
+        note_launches((long long)s->ctx->h_flag[3] * s->graph_iters[gi]);
         return;
     }
-    if (!s->graph[gi]) {
-        cudaGraph_t g;
-        MS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        g_capturing = true;
-        try {
-            for (int k = 0; k < kGraphIters; ++k) pcg_iteration<V>(s, v, prec);
-        } catch (...) {
-            g_capturing = false;
-            cudaStreamEndCapture(stream, &g);
-            throw;
-        }
-        g_capturing = false;
-        MS_CUDA(cudaStreamEndCapture(stream, &g));
-        size_t n_nodes = 0;
-        cudaGraphGetNodes(g, nullptr, &n_nodes);
-        s->graph_iters[gi] = (int)n_nodes;    // kernel nodes per replay
-        cudaError_t e = cudaGraphInstantiate(&s->graph[gi], g, 0);
-        cudaGraphDestroy(g);
-        MS_CUDA(e);
-    }
-    int done_iters = 0;
-    // first check after a short burst: small arrays converge in few iterations
-    while (done_iters < max_iter) {
-        MS_CUDA(cudaGraphLaunch(s->graph[gi], stream));
-        note_launches(s->graph_iters[gi]);
-        done_iters += kGraphIters;
-        MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    // no graph (legacy default stream, or conditional nodes unavailable):
+    // launch chunks of iterations and poll the any-active flag between them
+    for (int done_iters = 0; done_iters < max_iter + 2; done_iters += kChunkIters) {
+        for (int k = 0; k < kChunkIters; ++k) pcg_iteration<V>(s, v, prec, 0, 0, max_iter + 2);
+        MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
         MS_CUDA(cudaStreamSynchronize(stream));
         if (s->ctx->h_flag[0] == 0) break;
     }
 }
 
 // FP64 residual r = b - A x (a5) and the outer stopping test; returns whether
-// any array still needs a refinement step.
-bool outer_check(mstress_sol_s* s, int max_outer) {
+// any array still needs a refinement step. Y must be an FP64 element buffer.
+bool outer_check(mstress_sol_s* s, void* Y64, int max_outer) {
     cudaStream_t stream = s->ctx->stream;
     PcgVectors& v = s->v64;
-    launch_apply(s, MSTRESS_FP64, v.x.ptr, false, nullptr, s->Y.ptr);
-    launch_isum(s, s->Y.ptr, false, v.x.ptr, v.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
+    launch_apply(s, MSTRESS_FP64, v.x.ptr, nullptr, false, nullptr, Y64);
+    launch_isum(s, Y64, false, v.x.ptr, nullptr, v.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
     VecArgs va = vec_args(s, v);
     va.rhs = s->b.ptr;
     k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
@@ -781,7 +845,6 @@ struct LayoutIn {
 
 void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     mstress_ctx ctx = s->ctx;
-    // block models -> type table
     for (auto& li : in) {
         const mstress_layout* L = li.L;
         MS_REQUIRE(L, MSTRESS_EINVAL, "layout is NULL");
@@ -821,13 +884,14 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     configure_apply_kernels(ctx->device);
     s->n_el = t0->n_el;
     s->n_dof_block = t0->n_dof;
+    s->use_tc = s->precision != MSTRESS_FP64 && tc_supported(s->m);
     LocalMap lm = make_local_map(s->n);
     s->n_arrays = (int)in.size();
     const int n1 = s->n - 1;
 
     std::vector<BlockRef> bref;
     std::vector<VecWork> vwork;
-    std::vector<ApplyWork> awork;
+    std::vector<ApplyWork> awork, awork_tc;
     std::vector<int> blist;
     std::vector<uint8_t> fixed;
     std::vector<double> xbc;
@@ -853,7 +917,6 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         for (int64_t st = 0; st < A.n_dof; st += kVecChunk)
             vwork.push_back(VecWork{a, 0, vec_off + st, std::min<int64_t>(kVecChunk, A.n_dof - st)});
         A.n_vwork = (int)vwork.size() - A.vwork_off;
-        // type index of each site
         std::vector<int> tmap(L->n_blocks);
         for (int k = 0; k < L->n_blocks; ++k)
             tmap[k] = (int)(std::find(s->types.begin(), s->types.end(), L->blocks[k]) - s->types.begin());
@@ -866,13 +929,16 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
                 s->site.push_back((uint8_t)t);
                 per_type[t].push_back((int)e);
             }
+        // tiles of one type and one array: 32 blocks (CUDA-core kernels) and
+        // kTileTC blocks (tensor-core kernels) over the same block list
         for (int t = 0; t < s->n_types; ++t) {
             auto& v = per_type[t];
-            for (size_t st = 0; st < v.size(); st += kTile64) {
-                int cnt = (int)std::min<size_t>(kTile64, v.size() - st);
-                awork.push_back(ApplyWork{t, a, (int)blist.size(), cnt});
-                for (int k = 0; k < cnt; ++k) blist.push_back(v[st + k]);
-            }
+            const int start = (int)blist.size();
+            for (int e : v) blist.push_back(e);
+            for (size_t st = 0; st < v.size(); st += kTile64)
+                awork.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(kTile64, v.size() - st)});
+            for (size_t st = 0; st < v.size(); st += kTileTC)
+                awork_tc.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(kTileTC, v.size() - st)});
         }
         if (any_presc) {
             fixed.resize(vec_off + A.n_dof, 0);
@@ -896,6 +962,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     MS_REQUIRE(s->n_blocks < (1LL << 31), MSTRESS_EINVAL, "too many blocks");
     s->n_vwork = (int)vwork.size();
     s->n_awork = (int)awork.size();
+    s->n_awork_tc = (int)awork_tc.size();
 
     cudaStream_t st = ctx->stream;
     auto up = [&](DBuf& d, const void* src, size_t bytes) {
@@ -907,6 +974,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     up(s->d_bref, bref.data(), bref.size() * sizeof(BlockRef));
     up(s->d_blist, blist.data(), blist.size() * sizeof(int));
     up(s->d_awork, awork.data(), awork.size() * sizeof(ApplyWork));
+    up(s->d_awork_tc, awork_tc.data(), awork_tc.size() * sizeof(ApplyWork));
     up(s->d_vwork, vwork.data(), vwork.size() * sizeof(VecWork));
     up(s->d_site, s->site.data(), s->site.size());
     if (any_presc) {
@@ -931,10 +999,9 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     const bool mixed = s->precision != MSTRESS_FP64;
     alloc_into(ctx, s->Y, (size_t)s->n_blocks * s->ldY * (mixed ? sizeof(float) : sizeof(double)), false);
     if (mixed) {
-        // the FP64 residual needs an FP64 element buffer of its own
         for (int t = 0; t < s->n_types; ++t) {
             ensure_lowp(s->types[t], s->precision);
-            s->tt.Klp[t] = s->types[t]->Kr_lp[s->precision].ptr;
+            s->tt.Klp[t] = s->use_tc ? s->types[t]->Kr_tc[s->precision].ptr : s->types[t]->Kr_lp[s->precision].ptr;
         }
         alloc_into(ctx, s->v32.x, nv * sizeof(float));
         alloc_into(ctx, s->v32.r, nv * sizeof(float), false);
@@ -943,6 +1010,12 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         alloc_into(ctx, s->v32.q, nv * sizeof(float), false);
         alloc_into(ctx, s->v32.state, s->n_arrays * sizeof(PcgState));
     }
+}
+
+void check_device_error(mstress_sol_s* s) {
+    int f[4];
+    MS_CUDA(cudaMemcpy(f, s->flag.ptr, sizeof(f), cudaMemcpyDeviceToHost));
+    MS_REQUIRE(f[2] == 0, MSTRESS_EDEVICE_TIMEOUT, "a tensor-core wait timed out on the device");
 }
 
 void run_solve(mstress_sol_s* s) {
@@ -968,8 +1041,8 @@ void run_solve(mstress_sol_s* s) {
     if (mixed) alloc_into(ctx, Yfp64, (size_t)s->n_blocks * s->ldY * sizeof(double), false);
     void* Y64 = mixed ? Yfp64.ptr : s->Y.ptr;
     if (s->xbc.ptr) {   // lifting (Eq. 13): b -= A x_bc on the free DOFs
-        launch_apply(s, MSTRESS_FP64, s->xbc.ptr, false, nullptr, Y64);
-        launch_isum(s, Y64, false, s->xbc.ptr, s->v64.q.ptr, false, nullptr, nullptr, nullptr);
+        launch_apply(s, MSTRESS_FP64, s->xbc.ptr, nullptr, false, nullptr, Y64);
+        launch_isum(s, Y64, false, s->xbc.ptr, nullptr, s->v64.q.ptr, false, nullptr, nullptr, nullptr);
         k_lift_rhs<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->b.as<double>(),
                                                                             s->v64.q.as<double>(), s->dinv.as<double>());
         MS_LAUNCH_CHECK();
@@ -978,18 +1051,15 @@ void run_solve(mstress_sol_s* s) {
         pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_iter, nullptr);
         pcg_run<double>(s, s->v64, MSTRESS_FP64, o.max_iter);
     } else {
-        // a5: FP64-residual iterative refinement around a reduced-precision PCG.
-        // outer state: ||b||^2, x = 0, refinement-step count and limit
+        // a5: FP64-residual iterative refinement around a reduced-precision PCG;
+        // the outer state counts refinement steps against max_outer
         pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_outer, nullptr);
         int inner_total = 0;
         for (int k = 0; k <= o.max_outer; ++k) {
-            std::swap(s->Y, Yfp64);
-            bool more = outer_check(s, o.max_outer);
-            std::swap(s->Y, Yfp64);
-            if (!more) break;
-            pcg_start<float>(s, s->v32, s->v64.r.as<double>(), o.inner_rtol, std::max(1, o.max_iter - inner_total),
-                             s->v64.state.as<PcgState>());
-            pcg_run<float>(s, s->v32, s->precision, o.max_iter);
+            if (!outer_check(s, Y64, o.max_outer)) break;
+            const int budget = std::max(1, o.max_iter - inner_total);
+            pcg_start<float>(s, s->v32, s->v64.r.as<double>(), o.inner_rtol, budget, s->v64.state.as<PcgState>());
+            pcg_run<float>(s, s->v32, s->precision, budget);
             k_correct<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
                 s->d_vwork.as<VecWork>(), s->n_vwork, s->v64.state.as<PcgState>(), s->v64.x.as<double>(),
                 s->v32.x.as<float>());
@@ -1006,22 +1076,19 @@ void run_solve(mstress_sol_s* s) {
             inner_total = mx;
         }
     }
+    check_device_error(s);
     // true FP64 residual of the final iterate (and the outer count)
     {
         std::vector<PcgState> before(s->n_arrays);
         MS_CUDA(cudaMemcpyAsync(before.data(), s->v64.state.ptr, before.size() * sizeof(PcgState),
                                 cudaMemcpyDeviceToHost, stream));
-        MS_CUDA(cudaStreamSynchronize(stream));
-        if (mixed) std::swap(s->Y, Yfp64);
-        launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, false, nullptr, s->Y.ptr);
-        launch_isum(s, s->Y.ptr, false, s->v64.x.ptr, s->v64.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
+        launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, nullptr, false, nullptr, Y64);
+        launch_isum(s, Y64, false, s->v64.x.ptr, nullptr, s->v64.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
         VecArgs va = vec_args(s, s->v64);
         va.rhs = s->b.ptr;
-        // residual into z (scratch) so r keeps the recursive residual
-        va.r = s->v64.z.ptr;
+        va.r = s->v64.z.ptr;   // residual into z (scratch) so r keeps the recursive residual
         k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
         MS_LAUNCH_CHECK();
-        if (mixed) std::swap(s->Y, Yfp64);
         std::vector<double> prr(s->n_vwork);
         MS_CUDA(cudaMemcpyAsync(prr.data(), va.part_rr, prr.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
         MS_CUDA(cudaStreamSynchronize(stream));
@@ -1031,13 +1098,9 @@ void run_solve(mstress_sol_s* s) {
             for (int w = 0; w < A.n_vwork; ++w) rr += prr[A.vwork_off + w];
             ArrayResult& R = s->results[a];
             R.rel_res = before[a].bb > 0 ? std::sqrt(rr / before[a].bb) : 0.0;
-            if (mixed) {
-                R.outer = before[a].iters;
-                R.status = before[a].status;
-            } else {
-                R.iters = before[a].iters;
-                R.status = before[a].status;
-            }
+            if (mixed) R.outer = before[a].iters;
+            else R.iters = before[a].iters;
+            R.status = before[a].status;
             if (!std::isfinite(R.rel_res)) R.status = MSTRESS_ENUMERIC;
         }
     }
@@ -1147,8 +1210,9 @@ int mstress_apply(mstress_ctx ctx, const mstress_layout* layout, const double* x
     mstress_bc bc{1, 0, nullptr, nullptr, 0};
     std::vector<LayoutIn> in{LayoutIn{layout, 0.0, &bc}};
     validate_and_build(s.get(), in);
-    launch_apply(s.get(), MSTRESS_FP64, x_dev, false, nullptr, s->Y.ptr);
-    launch_isum(s.get(), s->Y.ptr, false, x_dev, y_dev, false, nullptr, nullptr, nullptr);
+    launch_apply(s.get(), MSTRESS_FP64, x_dev, nullptr, false, nullptr, s->Y.ptr);
+    launch_isum(s.get(), s->Y.ptr, false, const_cast<double*>(x_dev), nullptr, y_dev, false, nullptr, nullptr,
+                nullptr);
     MS_CUDA(cudaStreamSynchronize(ctx->stream));
     MS_API_END(ctx)
 }
@@ -1166,17 +1230,17 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
     auto run = [&]() {
         switch (phase) {
             case 0:
-                if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, true, nullptr, s->Y.ptr);
-                else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, false, nullptr, s->Y.ptr);
+                if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, nullptr, true, nullptr, s->Y.ptr);
+                else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, nullptr, false, nullptr, s->Y.ptr);
                 break;
             case 1:
-                if (mixed) launch_isum(s, s->Y.ptr, true, s->v32.p.ptr, s->v32.q.ptr, true, s->dinv.as<double>(),
-                                       nullptr, s->part.as<double>());
-                else launch_isum(s, s->Y.ptr, false, s->v64.p.ptr, s->v64.q.ptr, false, s->dinv.as<double>(),
+                if (mixed) launch_isum(s, s->Y.ptr, true, s->v32.p.ptr, nullptr, s->v32.q.ptr, true,
+                                       s->dinv.as<double>(), nullptr, s->part.as<double>());
+                else launch_isum(s, s->Y.ptr, false, s->v64.p.ptr, nullptr, s->v64.q.ptr, false, s->dinv.as<double>(),
                                  nullptr, s->part.as<double>());
                 break;
             case 2:
-                launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, false, nullptr, mixed ? y64.ptr : s->Y.ptr);
+                launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, nullptr, false, nullptr, mixed ? y64.ptr : s->Y.ptr);
                 break;
             case 3:
                 recover(s, MSTRESS_VM_ELEM, out.ptr, true);
@@ -1198,6 +1262,7 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *avg_ms = ms / reps;
+    check_device_error(s);
     MS_API_END(ctx)
 }
 

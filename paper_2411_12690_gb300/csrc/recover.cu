@@ -205,6 +205,7 @@ void ensure_lowp(mstress_block blk, int precision) {
     if (precision == MSTRESS_FP64) return;
     mstress_ctx ctx = blk->ctx;
     if (!blk->Kr_lp[precision].ptr) round_rows(ctx, blk->Kr_lp[precision], blk->Kr.as<double>(), blk->m, blk->m, blk->m, precision);
+    if (tc_supported(blk->m)) build_tc_operator(blk, precision);
     if (!blk->Smean_lp[precision].ptr)
         round_rows(ctx, blk->Smean_lp[precision], blk->Smean.as<double>(), (long long)6 * blk->n_el, blk->m1, blk->ld,
                    precision);

@@ -1,30 +1,73 @@
-// The resident solution of a (batched) global-stage solve and the launch
-// helpers the solve and recovery units share.
+// The resident solution of a (batched) global-stage solve and the device
+// helpers shared by the solve, tensor-core and recovery units.
 #pragma once
 
 #include "internal.h"
 
 namespace ms {
 
-constexpr int kVecChunk = 2048;   // lattice DOFs per vector work item
-constexpr int kTile64 = 32;       // blocks per FP64 apply / recovery tile
+constexpr int kVecChunk = 512;    // lattice DOFs per vector work item (2 per thread)
+constexpr int kTile64 = 32;       // blocks per CUDA-core apply / recovery tile
+constexpr int kTileTC = 128;      // blocks per tensor-core apply tile (the MMA M dimension)
 
 struct ArrayResult {
     int iters = 0, outer = 0, status = MSTRESS_OK;
     double rel_res = 0;
 };
 
-// Per-solve device scratch for one conjugate-gradient vector precision.
+// Per-solve device vectors for one conjugate-gradient precision.
 struct PcgVectors {
     DBuf x, r, z, p, q;   // packed lattice vectors of element type V
     DBuf state;           // PcgState per array
 };
+
+// Arguments of the element-product (operator apply) kernels.
+struct ApplyArgs {
+    const ApplyWork* work;
+    int n_work;
+    const int* blist;
+    const BlockRef* bref;
+    const ArrayDev* arrays;
+    const LocalMap* lm;
+    const PcgState* st;    // optional: skip stopped arrays; beta of the fused p update
+    TypeTab tt;
+    int m, ldY;
+    const void* x;         // vector gathered (p, or x for a plain product)
+    const void* z;         // optional: gather z + beta x instead of x
+    void* Y;               // element products [block][ldY]
+    int* err;              // device error word (bounded waits)
+};
+
+// The search-direction update p = z + beta p, written once so that the
+// gather of the apply and the interface sum compute identical bits.
+template <class V>
+__device__ __forceinline__ V p_next(V z, V p, double beta) {
+    return (V)fma(beta, (double)p, (double)z);
+}
+
+// Per-tile gather set-up: lattice base index of each block of the tile and
+// the per-array offset of each element DOF (Lagrange node (a, b, c) of the
+// block sits on lattice point (i(n-1)+a, j(n-1)+b, c)).
+__device__ __forceinline__ void tile_setup(const ApplyArgs& a, const ApplyWork& it, const ArrayDev& A,
+                                           long long* base, int* offs, int tile) {
+    const int n1 = a.lm->n - 1;
+    for (int k = threadIdx.x; k < a.m; k += blockDim.x) {
+        int q = k / 3, c = k - 3 * q;
+        offs[k] = ((a.lm->qc[q] * A.Y + a.lm->qb[q]) * A.X + a.lm->qa[q]) * 3 + c;
+    }
+    for (int t = threadIdx.x; t < tile; t += blockDim.x)
+        if (t < it.count) {
+            BlockRef br = a.bref[a.blist[it.start + t]];
+            base[t] = A.vec_off + 3LL * ((long long)br.j * n1 * A.X + (long long)br.i * n1);
+        }
+}
 
 }  // namespace ms
 
 struct mstress_sol_s {
     mstress_ctx ctx = nullptr;
     int precision = MSTRESS_FP64;
+    bool use_tc = false;                  // reduced-precision apply on tensor cores
     int n_arrays = 0, n_types = 0;
     int n = 0, m = 0, ldY = 0;
     int n_el = 0, n_dof_block = 0;
@@ -32,28 +75,37 @@ struct mstress_sol_s {
     std::vector<ms::ArrayDev> arrays;
     std::vector<mstress_block> types;     // not owned
     std::vector<uint8_t> site;            // type per block (global block order)
-    ms::DBuf d_lm, d_arrays, d_bref, d_blist, d_awork, d_vwork, d_site;
-    int n_awork = 0, n_vwork = 0;
+    ms::DBuf d_lm, d_arrays, d_bref, d_blist, d_awork, d_awork_tc, d_vwork, d_site;
+    int n_awork = 0, n_awork_tc = 0, n_vwork = 0;
     ms::DBuf b, dinv, fixed;              // FP64 right-hand side, Jacobi inverse (0 on constrained DOFs)
     ms::DBuf xbc;                         // prescribed values (lifting), or empty
     ms::PcgVectors v64, v32;              // FP64 outer / plain vectors, FP32 inner vectors
     ms::DBuf Y;                           // element-by-element products [block][ldY]
     ms::DBuf part;                        // 3 * n_vwork partial sums
-    ms::DBuf flag;                        // device int: any array still iterating
+    ms::DBuf flag;                        // device ints: any active, CTA ticket, error, loop count
     ms::TypeTab tt{};
     std::vector<ms::ArrayResult> results;
-    // captured CUDA graphs of the iteration loop, by vector precision (0: FP64, 1: FP32)
+    // CUDA graphs of the iteration loop (conditional WHILE node), by vector precision
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int graph_iters[2] = {0, 0};
+    int graph_iters[2] = {0, 0};          // kernel nodes per loop iteration
+    bool no_while[2] = {false, false};    // conditional nodes unavailable: chunked launches
     ~mstress_sol_s();
 };
 
 namespace ms {
 
-// global-stage kernels (online.cu)
-void launch_apply(mstress_sol_s* s, int prec, const void* x, bool vec_fp32, const PcgState* st, void* Y);
-void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, const void* p, void* q, bool vec_fp32,
+// global-stage launches (online.cu)
+ApplyArgs apply_args(mstress_sol_s* s, const void* x, const void* z, const PcgState* st, void* Y, bool tc);
+void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool vec_fp32, const PcgState* st,
+                  void* Y);
+void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, void* p, const void* z, void* q, bool vec_fp32,
                  const double* dinv, const PcgState* st, double* part_pq);
+
+// tensor-core kernels (tc.cu)
+bool tc_supported(int m);
+void configure_tc_kernels();
+void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a);
+void build_tc_operator(mstress_block blk, int prec);   // K_r image for the tensor-core apply
 
 // recovery (recover.cu)
 void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev);
