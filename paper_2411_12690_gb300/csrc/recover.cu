@@ -241,6 +241,9 @@ void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev) {
     }
     if (what == MSTRESS_LATTICE) {
         MS_CUDA(cudaMemcpyAsync(out, s->v64.x.ptr, bytes, cudaMemcpyDeviceToDevice, st));
+    } else if (what == MSTRESS_VM_ELEM && s->precision != MSTRESS_FP64 &&
+               tc_recover_supported(s->types[0]->m1, s->precision)) {
+        recover_vm_tc(s, static_cast<float*>(out));
     } else if (what == MSTRESS_COEFF) {
         long long n = s->n_blocks * s->m;
         k_coeff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->n_blocks, s->d_bref.as<BlockRef>(),

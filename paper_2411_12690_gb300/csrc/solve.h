@@ -107,6 +107,10 @@ void configure_tc_kernels();
 void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a);
 void build_tc_operator(mstress_block blk, int prec);   // K_r image for the tensor-core apply
 
+// tensor-core von Mises recovery (tc_recover.cu)
+bool tc_recover_supported(int m1, int prec);
+void recover_vm_tc(mstress_sol_s* s, float* out);
+
 // recovery (recover.cu)
 void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev);
 size_t recover_bytes(const mstress_sol_s* s, int what);
