@@ -1,0 +1,240 @@
+// Element-product (operator apply) work-item bodies, shared by the stand-alone
+// apply kernels and the persistent cooperative solver. A work item covers the
+// blocks of one tile (one block type, one array):
+//   apply64_item    FP64 on CUDA cores, one panel of 8*RPT rows of A_element
+//                   for 32 blocks (blockDim.x == 256)
+//   apply32_item    reduced precision on CUDA cores (fallback when the tensor
+//                   core tile does not fit), 32 blocks (blockDim.x == 256)
+//   apply_tc_item   tcgen05 tensor cores, up to 128 blocks (any multiple of 128 threads)
+// Every item gathers its blocks' element DOFs straight from the lattice
+// vector, optionally forming the search direction z + beta p on the fly.
+#pragma once
+
+#include "solve.h"
+#include "tc.cuh"
+
+namespace ms {
+namespace ai {
+
+__device__ __forceinline__ float round_tf32(float v) { return tc::to_tf32(v); }
+__device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+template <class V>
+__device__ __forceinline__ V gather(const V* x, const V* z, long long g, double beta) {
+    return z ? p_next(z[g], x[g], beta) : x[g];
+}
+
+// FP64 element products for one (32-block tile, row panel) item.
+// Shared: Cs [m][32], Ks [8*RPT][m]. The caller synchronises before reuse.
+template <int RPT>
+__device__ __forceinline__ void apply64_item(const ApplyArgs& a, const ApplyWork& it, int panel, double* Cs,
+                                             double* Ks, long long* base, int* offs) {
+    const int m = a.m;
+    const ArrayDev A = a.arrays[it.array];
+    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const double* __restrict__ x = static_cast<const double*>(a.x);
+    const double* __restrict__ z = static_cast<const double*>(a.z);
+    double* __restrict__ Y = static_cast<double*>(a.Y);
+    tile_setup(a, it, A, base, offs, kTile64);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * kTile64; idx += blockDim.x) {
+        const int k = idx >> 5, bt = idx & 31;
+        Cs[idx] = bt < it.count ? gather(x, z, base[bt] + offs[k], beta) : 0.0;
+    }
+    const double* __restrict__ K = a.tt.Kr[it.type];
+    const int r0 = panel * 8 * RPT;
+    const int rows = min(8 * RPT, m - r0);
+    for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += blockDim.x)
+        Ks[idx] = idx < rows * m ? K[(size_t)r0 * m + idx] : 0.0;
+    __syncthreads();
+    const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
+    double acc[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) acc[u] = 0;
+    const double* kr = Ks + rg * RPT * m;
+    for (int k = 0; k < m; ++k) {
+        const double c = Cs[k * kTile64 + bt];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) acc[u] = fma(kr[u * m + k], c, acc[u]);
+    }
+    if (bt < it.count) {
+        const long long e = a.blist[it.start + bt];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int r = r0 + rg * RPT + u;
+            if (r < m) Y[e * a.ldY + r] = acc[u];
+        }
+    }
+}
+
+// Reduced-precision element products on CUDA cores for one (32-block tile,
+// row panel) item. Klp holds K rounded to the operand format (as float;
+// BF16X3: [K_hi; K_lo]); the gathered coefficients are rounded the same way
+// and the products accumulate in FP32, as on the tensor cores.
+template <int RPT, int MODE>
+__device__ __forceinline__ void apply32_item(const ApplyArgs& a, const ApplyWork& it, int panel, float* Cs, float* Ks,
+                                             long long* base, int* offs) {
+    constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
+    const int m = a.m;
+    const ArrayDev A = a.arrays[it.array];
+    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    const float* __restrict__ z = static_cast<const float*>(a.z);
+    float* __restrict__ Y = static_cast<float*>(a.Y);
+    tile_setup(a, it, A, base, offs, kTile64);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * kTile64; idx += blockDim.x) {
+        const int k = idx >> 5, bt = idx & 31;
+        const float v = bt < it.count ? gather(x, z, base[bt] + offs[k], beta) : 0.0f;
+        if (MODE == MSTRESS_TF32) Cs[idx] = round_tf32(v);
+        else if (MODE == MSTRESS_BF16) Cs[idx] = round_bf16(v);
+        else {
+            const float hi = round_bf16(v);
+            Cs[idx] = hi;
+            Cs[(size_t)m * kTile64 + idx] = round_bf16(v - hi);
+        }
+    }
+    const float* __restrict__ K = static_cast<const float*>(a.tt.Klp[it.type]);
+    const int r0 = panel * 8 * RPT;
+    const int rows = min(8 * RPT, m - r0);
+    for (int s = 0; s < NS; ++s)
+        for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += blockDim.x)
+            Ks[(size_t)s * 8 * RPT * m + idx] = idx < rows * m ? K[(size_t)s * m * m + (size_t)r0 * m + idx] : 0.0f;
+    __syncthreads();
+    const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
+    float acc[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) acc[u] = 0;
+    const float* kr = Ks + rg * RPT * m;
+    const float* krl = kr + (size_t)8 * RPT * m;
+    for (int k = 0; k < m; ++k) {
+        const float c = Cs[k * kTile64 + bt];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) acc[u] = fmaf(kr[u * m + k], c, acc[u]);
+        if (NS == 2) {
+            const float cl = Cs[(size_t)m * kTile64 + k * kTile64 + bt];
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) acc[u] = fmaf(kr[u * m + k], cl, fmaf(krl[u * m + k], c, acc[u]));
+        }
+    }
+    if (bt < it.count) {
+        const long long e = a.blist[it.start + bt];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int r = r0 + rg * RPT + u;
+            if (r < m) Y[e * a.ldY + r] = acc[u];
+        }
+    }
+}
+
+// ------------------------------------------------------- tensor cores
+struct TcShape {
+    int m, esz, kpad, npad, ksteps, tmem_cols, ns;
+    uint32_t a_plane, b_plane;   // bytes per operand plane (multiples of 1024)
+    size_t smem;                 // dynamic shared memory of a CTA using this shape
+};
+
+}  // namespace ai
+
+ai::TcShape tc_shape(int m, int prec);   // tensor-core apply tile geometry (tc.cu)
+
+namespace ai {
+
+__device__ __forceinline__ void put_operand(uint8_t* plane0, uint32_t plane_bytes, uint32_t off, float v, int mode) {
+    if (mode == MSTRESS_TF32) {
+        *reinterpret_cast<float*>(plane0 + off) = tc::to_tf32(v);
+    } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(plane0 + off) = hi;
+        if (mode == MSTRESS_BF16X3)
+            *reinterpret_cast<__nv_bfloat16*>(plane0 + plane_bytes + off) =
+                __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+// Per-CTA tensor-core state that persists across work items.
+struct TcState {
+    uint8_t* sA;        // gathered coefficients (NS planes)
+    uint8_t* sB;        // operator image of the current type (NS planes)
+    uint64_t* mbar;
+    uint32_t tmem;
+    uint32_t phase;
+    int cur_type;
+};
+
+// D (128 x npad) = C (tile blocks x K) * K_r^T on the tensor cores for one
+// tile; writes the element products Y of the tile's blocks. Returns false if
+// the MMA completion wait timed out (the caller stops and reports it).
+template <int MODE>
+__device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape& sh, const ApplyWork& it,
+                                              TcState& ts, long long* base, int* offs) {
+    constexpr bool TF32 = MODE == MSTRESS_TF32;
+    constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const int m = a.m;
+    const ArrayDev A = a.arrays[it.array];
+    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    const float* __restrict__ z = static_cast<const float*>(a.z);
+    float* __restrict__ Y = static_cast<float*>(a.Y);
+    if (it.type != ts.cur_type) {
+        const uint4* src = static_cast<const uint4*>(a.tt.Klp[it.type]);
+        for (uint32_t i = tid; i < NS * sh.b_plane / 16; i += blockDim.x) reinterpret_cast<uint4*>(ts.sB)[i] = src[i];
+        ts.cur_type = it.type;
+    }
+    tile_setup(a, it, A, base, offs, kTileTC);
+    __syncthreads();
+    for (int idx = tid; idx < m * kTileTC; idx += blockDim.x) {
+        const int k = idx >> 7, b = idx & (kTileTC - 1);
+        const float v = b < it.count ? gather(x, z, base[b] + offs[k], beta) : 0.0f;
+        put_operand(ts.sA, sh.a_plane, tc::operand_offset(b, k, sh.kpad, sh.esz), v, MODE);
+    }
+    tc::fence_smem_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+        const uint32_t idesc = tc::instr_desc(TF32, kTileTC, sh.npad);
+        const uint32_t sbo = tc::sbo_bytes(sh.kpad, sh.esz);
+        const uint32_t a0 = tc::smem_addr(ts.sA), b0 = tc::smem_addr(ts.sB);
+        uint32_t acc = 0;
+        for (int s = 0; s < sh.ksteps; ++s) {
+            const uint32_t ko = (uint32_t)s * 2 * tc::kLBO;
+            // products (A plane, B plane): (hi, hi) [, (lo, hi), (hi, lo)]
+#pragma unroll
+            for (int pr = 0; pr < (NS == 2 ? 3 : 1); ++pr) {
+                const uint32_t pa = pr == 1 ? sh.a_plane : 0u, pb = pr == 2 ? sh.b_plane : 0u;
+                tc::mma<TF32>(ts.tmem, tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo),
+                              tc::smem_desc(b0 + pb + ko, tc::kLBO, sbo), idesc, acc);
+                acc = 1;
+            }
+        }
+        tc::commit(ts.mbar);
+    }
+    const bool ok = tc::mbar_wait(ts.mbar, ts.phase, 1 << 24);
+    ts.phase ^= 1u;
+    tc::fence_after();
+    if (__syncthreads_or(!ok)) return false;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one block each) and
+    // column chunks 16 (w / 4), 16 (w / 4 + nw / 4), ...
+    const int b = (warp & 3) * 32 + lane;
+    const long long e = b < it.count ? a.blist[it.start + b] : 0;
+    for (int c0 = 16 * (warp >> 2); c0 < sh.npad; c0 += 16 * (nw >> 2)) {
+        float v[16];
+        tc::tmem_ld16(ts.tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
+        if (b < it.count && c0 < a.ldY) {
+            float4* dst = reinterpret_cast<float4*>(Y + e * a.ldY + c0);
+            dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+            dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+            dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+            dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return true;
+}
+
+}  // namespace ai
+}  // namespace ms

@@ -98,6 +98,7 @@ struct VecWork { int array, pad; long long start, count; };  // packed lattice D
 struct PcgState {            // per-array conjugate-gradient scalars
     double rz, rr, bb, tol2;
     double beta;             // pending p = z + beta p of the next iteration
+    double alpha;            // step length of the current iteration (persistent solver)
     int iters, active, status, max_iter;
 };
 

@@ -523,6 +523,9 @@ struct ScalarArgs {
 
 __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ ScalarArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
     int any = 0;
     for (int k = warp; k < a.n_arrays; k += 32) {
         const ArrayDev A = a.arrays[k];
@@ -556,13 +559,17 @@ __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ Scalar
                 a.st[k] = s;
             }
         }
-        if (lane == 0) any |= a.st[k].active;
+        if (lane == 0 && a.st[k].active) {
+            any = 1;
+            atomicAdd(&s_count, 1);
+        }
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
         a.flag[0] = any;
         a.flag[1] = 0;
         a.flag[3] = 0;
+        a.flag[4] = s_count;   // arrays active (persistent solver)
     }
 }
 
@@ -799,6 +806,11 @@ void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
     constexpr int gi = std::is_same<V, float>::value ? 1 : 0;
     cudaStream_t stream = s->ctx->stream;
     int* flag = s->flag.as<int>();
+    // preferred: one persistent cooperative launch for the whole run
+    if (pcg_run_persistent(s, v, prec, max_iter, std::is_same<V, float>::value)) {
+        MS_CUDA(cudaStreamSynchronize(stream));
+        return;
+    }
     if (stream != nullptr && !s->graph[gi] && !s->no_while[gi]) s->no_while[gi] = !build_while_graph<V>(s, v, prec, gi, max_iter);
     if (s->graph[gi]) {
         MS_CUDA(cudaGraphLaunch(s->graph[gi], stream));
@@ -996,6 +1008,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     alloc_into(ctx, s->v64.state, s->n_arrays * sizeof(PcgState));
     alloc_into(ctx, s->part, 3 * (size_t)s->n_vwork * sizeof(double));
     alloc_into(ctx, s->flag, 64);
+    alloc_into(ctx, s->tickets, 2 * (size_t)s->n_arrays * sizeof(int));
     const bool mixed = s->precision != MSTRESS_FP64;
     alloc_into(ctx, s->Y, (size_t)s->n_blocks * s->ldY * (mixed ? sizeof(float) : sizeof(double)), false);
     if (mixed) {

@@ -82,7 +82,9 @@ struct mstress_sol_s {
     ms::PcgVectors v64, v32;              // FP64 outer / plain vectors, FP32 inner vectors
     ms::DBuf Y;                           // element-by-element products [block][ldY]
     ms::DBuf part;                        // 3 * n_vwork partial sums
-    ms::DBuf flag;                        // device ints: any active, CTA ticket, error, loop count
+    ms::DBuf flag;                        // device ints: [0] any active, [1] CTA ticket, [2] error,
+                                          // [3] loop count, [4] arrays active, [5..6] grid barrier, [7] abort
+    ms::DBuf tickets;                     // 2 ints per array (persistent solver folds)
     ms::TypeTab tt{};
     std::vector<ms::ArrayResult> results;
     // CUDA graphs of the iteration loop (conditional WHILE node), by vector precision
@@ -100,6 +102,9 @@ void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool
                   void* Y);
 void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, void* p, const void* z, void* q, bool vec_fp32,
                  const double* dinv, const PcgState* st, double* part_pq);
+
+// persistent cooperative PCG (pcg_persistent.cu); false if it cannot be launched
+bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter, bool vec_fp32);
 
 // tensor-core kernels (tc.cu)
 bool tc_supported(int m);

@@ -1,0 +1,72 @@
+"""Batched solves of uneven arrays (mstress_solve_batch): every array's result
+is the same alone and inside the batch (bitwise: an array's arithmetic never
+depends on the other arrays), and matches the oracle."""
+import numpy as np
+import pytest
+
+from cases import SMALL_MESH, oracle_solve, rel_l2
+from oracle import mor
+from paper_2411_12690_gb300 import _lib as L
+from paper_2411_12690_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2411_12690_gb300 import api, build
+    build.build()
+    return api
+
+
+def _per_array(sol, sizes, what, width):
+    out = sol.recover(what)
+    res, off = [], 0
+    for s in sizes:
+        res.append(out[off:off + s * width].copy())
+        off += s * width
+    return res
+
+
+@pytest.mark.parametrize("prec", [L.MSTRESS_FP64, L.MSTRESS_BF16X3, L.MSTRESS_TF32])
+def test_batch_equals_alone(api, prec):
+    ctx = api.Context(precision=prec)
+    blks = [ctx.build_block(SMALL_MESH), ctx.build_block(SMALL_MESH.dummy())]
+    rng = np.random.default_rng(5)
+    jobs = []
+    for k, (nx, ny) in enumerate([(1, 1), (3, 2), (7, 5), (2, 9), (12, 12), (4, 4)]):
+        st = W.site_types(nx, ny, 0.7, seed=10 + k)
+        jobs.append(dict(site_type=st, blocks=blks, dT=float(rng.uniform(-300, -150)), clamp_top=(k == 3)))
+    batch = ctx.solve_batch(jobs)
+    n_el = SMALL_MESH.ex * SMALL_MESH.ey * SMALL_MESH.ez
+    m = 78
+    sizes = [j["site_type"].size for j in jobs]
+    bc = _per_array(batch, sizes, L.MSTRESS_COEFF, m)
+    bv = _per_array(batch, sizes, L.MSTRESS_VM_ELEM, n_el)
+    for k, j in enumerate(jobs):
+        alone = ctx.solve(j["site_type"], blks, j["dT"], clamp_top=j["clamp_top"])
+        assert alone.info()["status"] == 0 and batch.info(k)["status"] == 0
+        assert batch.info(k)["iters"] == alone.info()["iters"]
+        assert np.array_equal(alone.recover(L.MSTRESS_COEFF), bc[k])
+        assert np.array_equal(alone.recover(L.MSTRESS_VM_ELEM), bv[k])
+        if prec == L.MSTRESS_FP64:
+            ob, osol = oracle_solve(SMALL_MESH, j["site_type"], j["dT"], clamp_top=j["clamp_top"])
+            assert rel_l2(bc[k].reshape(-1, m), osol.coeffs) <= 1e-9
+            assert rel_l2(bv[k].reshape(-1, n_el), mor.recover_vm(ob, osol)) <= 1e-9
+
+
+def test_batch_two_block_variants_m294(api):
+    """Degree-4 basis (m = 294), 24x24x20 meshes, two pitch variants, each
+    with its dummy block, in one batch; results equal the single-array solves."""
+    ctx = api.Context(precision=L.MSTRESS_BF16X3)
+    variants = [W.BLOCK_P15, W.BLOCK_P20]
+    models = [[ctx.build_block(v), ctx.build_block(v.dummy())] for v in variants]
+    jobs = W.batch_arrays(5, seed=3, smin=2, smax=6)
+    spec = [dict(site_type=j.site_type, blocks=models[j.pitch], dT=j.dT) for j in jobs]
+    batch = ctx.solve_batch(spec)
+    sizes = [j.site_type.size for j in jobs]
+    bc = _per_array(batch, sizes, L.MSTRESS_COEFF, 294)
+    for k, j in enumerate(spec):
+        alone = ctx.solve(j["site_type"], j["blocks"], j["dT"])
+        assert np.array_equal(alone.recover(L.MSTRESS_COEFF), bc[k])
+        assert batch.info(k)["rel_res"] <= 1e-12
