@@ -24,6 +24,35 @@ __device__ __forceinline__ V gather(const V* x, const V* z, long long g, double 
     return z ? p_next(z[g], x[g], beta) : x[g];
 }
 
+// Gather the element DOFs of a tile of (1 << tile_shift) blocks, index
+// idx = k * tile + b, eight values per thread in flight at a time (the loads of
+// a round are independent, so they overlap instead of queueing one L2 round
+// trip behind another). store(idx, k, b, v) writes one value.
+template <class V, class Store>
+__device__ __forceinline__ void gather_tile(const V* __restrict__ x, const V* __restrict__ z, double beta, int m,
+                                            int tile_shift, int count, const long long* base, const int* offs,
+                                            Store store) {
+    constexpr int GU = 8;
+    const int total = m << tile_shift, mask = (1 << tile_shift) - 1;
+    for (int idx0 = threadIdx.x; idx0 < total; idx0 += blockDim.x * GU) {
+        V v[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = idx0 + u * blockDim.x;
+            v[u] = V(0);
+            if (idx < total) {
+                const int k = idx >> tile_shift, b = idx & mask;
+                if (b < count) v[u] = gather(x, z, base[b] + offs[k], beta);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = idx0 + u * blockDim.x;
+            if (idx < total) store(idx, idx >> tile_shift, idx & mask, v[u]);
+        }
+    }
+}
+
 // FP64 element products for one (32-block tile, row panel) item.
 // Shared: Cs [m][32], Ks [8*RPT][m]. The caller synchronises before reuse.
 template <int RPT>
@@ -37,10 +66,7 @@ __device__ __forceinline__ void apply64_item(const ApplyArgs& a, const ApplyWork
     double* __restrict__ Y = static_cast<double*>(a.Y);
     tile_setup(a, it, A, base, offs, kTile64);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < m * kTile64; idx += blockDim.x) {
-        const int k = idx >> 5, bt = idx & 31;
-        Cs[idx] = bt < it.count ? gather(x, z, base[bt] + offs[k], beta) : 0.0;
-    }
+    gather_tile(x, z, beta, m, 5, it.count, base, offs, [&](int idx, int, int, double v) { Cs[idx] = v; });
     const double* __restrict__ K = a.tt.Kr[it.type];
     const int r0 = panel * 8 * RPT;
     const int rows = min(8 * RPT, m - r0);
@@ -83,9 +109,7 @@ __device__ __forceinline__ void apply32_item(const ApplyArgs& a, const ApplyWork
     float* __restrict__ Y = static_cast<float*>(a.Y);
     tile_setup(a, it, A, base, offs, kTile64);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < m * kTile64; idx += blockDim.x) {
-        const int k = idx >> 5, bt = idx & 31;
-        const float v = bt < it.count ? gather(x, z, base[bt] + offs[k], beta) : 0.0f;
+    gather_tile(x, z, beta, m, 5, it.count, base, offs, [&](int idx, int, int, float v) {
         if (MODE == MSTRESS_TF32) Cs[idx] = round_tf32(v);
         else if (MODE == MSTRESS_BF16) Cs[idx] = round_bf16(v);
         else {
@@ -93,7 +117,7 @@ __device__ __forceinline__ void apply32_item(const ApplyArgs& a, const ApplyWork
             Cs[idx] = hi;
             Cs[(size_t)m * kTile64 + idx] = round_bf16(v - hi);
         }
-    }
+    });
     const float* __restrict__ K = static_cast<const float*>(a.tt.Klp[it.type]);
     const int r0 = panel * 8 * RPT;
     const int rows = min(8 * RPT, m - r0);
@@ -184,11 +208,9 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     }
     tile_setup(a, it, A, base, offs, kTileTC);
     __syncthreads();
-    for (int idx = tid; idx < m * kTileTC; idx += blockDim.x) {
-        const int k = idx >> 7, b = idx & (kTileTC - 1);
-        const float v = b < it.count ? gather(x, z, base[b] + offs[k], beta) : 0.0f;
+    gather_tile(x, z, beta, m, 7, it.count, base, offs, [&](int, int k, int b, float v) {
         put_operand(ts.sA, sh.a_plane, tc::operand_offset(b, k, sh.kpad, sh.esz), v, MODE);
-    }
+    });
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();

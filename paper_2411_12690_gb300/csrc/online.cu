@@ -30,77 +30,17 @@
 #include <cstdio>
 #include <type_traits>
 
-#include "solve.h"
+#include "apply_items.cuh"
+#include "pcg_items.cuh"
 
 namespace ms {
 namespace {
 
 constexpr int kThreads = 256;
-
-// ----------------------------------------------------------- reductions
-// Fixed-order sum of n values by one warp: lane-strided partial sums, then a
-// butterfly. Every caller that folds the same array gets the same bits. Loads
-// bypass L1 because the values come from other CTAs.
-__device__ __forceinline__ double warp_fold(const double* v, int n) {
-    const int lane = threadIdx.x & 31;
-    double s = 0;
-    int i = lane;
-    for (; i + 96 < n; i += 128) {   // four loads in flight, summed in index order
-        const double a0 = __ldcg(v + i), a1 = __ldcg(v + i + 32), a2 = __ldcg(v + i + 64), a3 = __ldcg(v + i + 96);
-        s += a0;
-        s += a1;
-        s += a2;
-        s += a3;
-    }
-    for (; i < n; i += 32) s += __ldcg(v + i);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
-// Block sum (kThreads threads) in a fixed order; result valid in all threads.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0;
-    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
-    return t;
-}
-
-__device__ __forceinline__ void lattice_coords(const ArrayDev& A, long long g, int& comp, int& gx, int& gy,
-                                               int& gz) {
-    // an array's lattice holds fewer than 2^31 DOFs, so 32-bit division suffices
-    const unsigned l = (unsigned)(g - A.vec_off);
-    const unsigned node = l / 3u;
-    comp = (int)(l - 3u * node);
-    const unsigned X = (unsigned)A.X, t = node / X;
-    gx = (int)(node - t * X);
-    const unsigned Y = (unsigned)A.Y, zz = t / Y;
-    gy = (int)(t - zz * Y);
-    gz = (int)zz;
-}
-
-// Visit the blocks that own lattice point (gx, gy, gz) with the point's
-// surface-node index there, rows ascending then columns ascending.
-template <class Fn>
-__device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __restrict__ surf, int n, int gx,
-                                           int gy, int gz, Fn fn) {
-    const int n1 = n - 1;
-    int ih = gx / n1, il = (gx % n1 == 0) ? ih - 1 : ih;
-    int jh = gy / n1, jl = (gy % n1 == 0) ? jh - 1 : jh;
-    ih = min(ih, A.nx - 1);
-    jh = min(jh, A.ny - 1);
-    il = max(il, 0);
-    jl = max(jl, 0);
-    for (int j = jl; j <= jh; ++j)
-        for (int i = il; i <= ih; ++i) {
-            int a = gx - i * n1, b = gy - j * n1;
-            int s = __ldg(surf + (gz * n + b) * n + a);
-            if (s >= 0) fn(A.block_off + (long long)j * A.nx + i, s);
-        }
-}
+using pi::block_sum;
+using pi::for_owners;
+using pi::lattice_coords;
+using pi::warp_fold;
 
 // ---------------------------------------------------------- a2: rhs, diag
 struct RhsArgs {
@@ -141,148 +81,37 @@ __global__ void __launch_bounds__(kThreads) k_rhs_diag(const __grid_constant__ R
 }
 
 // ------------------------------------------------------ a3: operator apply
-// FP64 element products. A work item is one panel of 8*RPT rows of A_element
-// for a tile of 32 blocks of one type and one array, so that the items (and
-// the FP64 work) spread evenly over the SMs. Shared: C [m][32] (gathered
-// coefficients), K panel [8*RPT][m].
+// Element products on CUDA cores; a work item is one panel of 8*RPT rows of
+// A_element for a 32-block tile of one type and one array (apply_items.cuh),
+// so the items spread evenly over the SMs. Shared: C [NS][m][32], K panel.
 template <int RPT>
 __global__ void __launch_bounds__(kThreads) k_apply64(const __grid_constant__ ApplyArgs a) {
     extern __shared__ double sm[];
     __shared__ long long base[kTile64];
     __shared__ int offs[3 * kMaxSurf];
-    const int m = a.m;
-    const int n_panels = (m + 8 * RPT - 1) / (8 * RPT);
-    double* Cs = sm;
-    double* Ks = sm + (size_t)m * kTile64;
-    const double* __restrict__ x = static_cast<const double*>(a.x);
-    const double* __restrict__ z = static_cast<const double*>(a.z);
-    double* __restrict__ Y = static_cast<double*>(a.Y);
+    const int n_panels = (a.m + 8 * RPT - 1) / (8 * RPT);
     for (int w = blockIdx.x; w < a.n_work * n_panels; w += gridDim.x) {
         const ApplyWork it = a.work[w / n_panels];
-        const int panel = w % n_panels;
         if (a.st && !a.st[it.array].active) continue;
-        const ArrayDev A = a.arrays[it.array];
-        const double beta = a.st ? a.st[it.array].beta : 0.0;
         __syncthreads();
-        tile_setup(a, it, A, base, offs, kTile64);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < m * kTile64; idx += kThreads) {
-            int k = idx >> 5, bt = idx & 31;
-            double v = 0.0;
-            if (bt < it.count) {
-                long long g = base[bt] + offs[k];
-                v = z ? p_next(z[g], x[g], beta) : x[g];
-            }
-            Cs[idx] = v;
-        }
-        const double* __restrict__ K = a.tt.Kr[it.type];
-        const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
-        const int r0 = panel * 8 * RPT;
-        const int rows = min(8 * RPT, m - r0);
-        for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += kThreads)
-            Ks[idx] = idx < rows * m ? K[(size_t)r0 * m + idx] : 0.0;
-        __syncthreads();
-        double acc[RPT];
-#pragma unroll
-        for (int u = 0; u < RPT; ++u) acc[u] = 0;
-        const double* kr = Ks + rg * RPT * m;
-        for (int k = 0; k < m; ++k) {
-            double c = Cs[k * kTile64 + bt];
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) acc[u] = fma(kr[u * m + k], c, acc[u]);
-        }
-        if (bt < it.count) {
-            const long long e = a.blist[it.start + bt];
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                int r = r0 + rg * RPT + u;
-                if (r < m) Y[e * a.ldY + r] = acc[u];
-            }
-        }
+        ai::apply64_item<RPT>(a, it, w % n_panels, sm, sm + (size_t)a.m * kTile64, base, offs);
     }
 }
 
 // Reduced-precision element products on CUDA cores (FP32 vectors), used when
-// the tensor-core path does not cover the basis size. The operator copy Klp
-// holds K rounded to the mode's operand format (stored as float); BF16X3 holds
-// [K_hi; K_lo]. The gathered coefficients are rounded the same way and the
-// products accumulate in FP32, as on the tensor cores.
-__device__ __forceinline__ float round_tf32(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
-}
-__device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-
+// the tensor-core tile does not cover the basis size.
 template <int RPT, int MODE>
 __global__ void __launch_bounds__(kThreads) k_apply32(const __grid_constant__ ApplyArgs a) {
     extern __shared__ float smf[];
     __shared__ long long base[kTile64];
     __shared__ int offs[3 * kMaxSurf];
-    const int m = a.m;
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
-    float* Cs = smf;                                   // [NS][m][32]
-    float* Ks = smf + (size_t)NS * m * kTile64;        // [NS][8*RPT][m]
-    const float* __restrict__ x = static_cast<const float*>(a.x);
-    const float* __restrict__ z = static_cast<const float*>(a.z);
-    float* __restrict__ Y = static_cast<float*>(a.Y);
-    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
-        const ApplyWork it = a.work[w];
+    const int n_panels = (a.m + 8 * RPT - 1) / (8 * RPT);
+    for (int w = blockIdx.x; w < a.n_work * n_panels; w += gridDim.x) {
+        const ApplyWork it = a.work[w / n_panels];
         if (a.st && !a.st[it.array].active) continue;
-        const ArrayDev A = a.arrays[it.array];
-        const double beta = a.st ? a.st[it.array].beta : 0.0;
         __syncthreads();
-        tile_setup(a, it, A, base, offs, kTile64);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < m * kTile64; idx += kThreads) {
-            int k = idx >> 5, bt = idx & 31;
-            float v = 0.0f;
-            if (bt < it.count) {
-                long long g = base[bt] + offs[k];
-                v = z ? p_next(z[g], x[g], beta) : x[g];
-            }
-            if (MODE == MSTRESS_TF32) Cs[idx] = round_tf32(v);
-            else if (MODE == MSTRESS_BF16) Cs[idx] = round_bf16(v);
-            else {
-                float hi = round_bf16(v);
-                Cs[idx] = hi;
-                Cs[(size_t)m * kTile64 + idx] = round_bf16(v - hi);
-            }
-        }
-        const float* __restrict__ K = static_cast<const float*>(a.tt.Klp[it.type]);
-        const int rg = threadIdx.x >> 5, bt = threadIdx.x & 31;
-        for (int r0 = 0; r0 < m; r0 += 8 * RPT) {
-            __syncthreads();
-            const int rows = min(8 * RPT, m - r0);
-            for (int s = 0; s < NS; ++s)
-                for (int idx = threadIdx.x; idx < 8 * RPT * m; idx += kThreads)
-                    Ks[(size_t)s * 8 * RPT * m + idx] =
-                        idx < rows * m ? K[(size_t)s * m * m + (size_t)r0 * m + idx] : 0.0f;
-            __syncthreads();
-            float acc[RPT];
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) acc[u] = 0;
-            const float* kr = Ks + rg * RPT * m;
-            for (int k = 0; k < m; ++k) {
-                float c = Cs[k * kTile64 + bt];
-#pragma unroll
-                for (int u = 0; u < RPT; ++u) acc[u] = fmaf(kr[u * m + k], c, acc[u]);
-                if (NS == 2) {
-                    float cl = Cs[(size_t)m * kTile64 + k * kTile64 + bt];
-                    const float* krl = kr + (size_t)8 * RPT * m;
-#pragma unroll
-                    for (int u = 0; u < RPT; ++u) acc[u] = fmaf(kr[u * m + k], cl, fmaf(krl[u * m + k], c, acc[u]));
-                }
-            }
-            if (bt < it.count) {
-                const long long e = a.blist[it.start + bt];
-#pragma unroll
-                for (int u = 0; u < RPT; ++u) {
-                    int r = r0 + rg * RPT + u;
-                    if (r < m) Y[e * a.ldY + r] = acc[u];
-                }
-            }
-        }
+        ai::apply32_item<RPT, MODE>(a, it, w % n_panels, smf, smf + (size_t)NS * a.m * kTile64, base, offs);
     }
 }
 
@@ -306,35 +135,16 @@ struct IsumArgs {
 template <class V, class YT>
 __global__ void __launch_bounds__(kThreads) k_isum(const __grid_constant__ IsumArgs a) {
     __shared__ double sh[kThreads / 32];
-    const YT* __restrict__ Y = static_cast<const YT*>(a.Y);
-    V* __restrict__ p = static_cast<V*>(a.p);
-    const V* __restrict__ z = static_cast<const V*>(a.z);
-    V* __restrict__ q = static_cast<V*>(a.q);
     for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
         const VecWork it = a.vwork[w];
         if (a.st && !a.st[it.array].active) continue;
         const ArrayDev A = a.arrays[it.array];
         const double beta = a.st ? a.st[it.array].beta : 0.0;
-        double acc = 0;
-        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
-            double s = 0;
-            if (!a.dinv || a.dinv[g] != 0.0) {
-                int comp, gx, gy, gz;
-                lattice_coords(A, g, comp, gx, gy, gz);
-                for_owners(A, a.lm->surf_idx, a.lm->n, gx, gy, gz, [&](long long blk, int sidx) {
-                    s += (double)Y[blk * a.ldY + 3 * sidx + comp];
-                });
-            }
-            V pv = p[g];
-            if (z) {
-                pv = p_next(z[g], pv, beta);
-                p[g] = pv;
-            }
-            q[g] = (V)s;
-            acc += (double)pv * s;
-        }
+        const double acc = pi::isum_item<V, YT>(it, A, a.lm, a.dinv, a.ldY, static_cast<const YT*>(a.Y),
+                                                static_cast<V*>(a.p), static_cast<const V*>(a.z),
+                                                static_cast<V*>(a.q), beta);
         if (a.part_pq) {
-            double t = block_sum(acc, sh);
+            const double t = block_sum(acc, sh);
             if (threadIdx.x == 0) a.part_pq[w] = t;
         }
     }
@@ -407,17 +217,8 @@ __global__ void __launch_bounds__(kThreads) k_vec1(const __grid_constant__ VecAr
         }
         __syncthreads();
         const double al = s_alpha;
-        double srz = 0, srr = 0;
-        for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += kThreads) {
-            double pv = (double)p[g], qv = (double)q[g];
-            x[g] = (V)((double)x[g] + al * pv);
-            V rv = (V)((double)r[g] - al * qv);
-            V zv = (V)(a.dinv[g] * (double)rv);
-            r[g] = rv;
-            z[g] = zv;
-            srz += (double)rv * (double)zv;
-            srr += (double)rv * (double)rv;
-        }
+        double srz, srr;
+        pi::vec1_item<V>(it, a.dinv, al, x, r, z, p, q, srz, srr);
         srz = block_sum(srz, sh);
         srr = block_sum(srr, sh);
         if (threadIdx.x == 0) { a.part_rz[w] = srz; a.part_rr[w] = srr; }
@@ -588,9 +389,9 @@ void configure_apply_kernels(int device) {
     auto set = [](auto k) { MS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)); };
     set(k_apply64<2>);
     set(k_apply64<4>);
-    set(k_apply32<10, MSTRESS_TF32>);
-    set(k_apply32<10, MSTRESS_BF16>);
-    set(k_apply32<10, MSTRESS_BF16X3>);
+    set(k_apply32<2, MSTRESS_TF32>);
+    set(k_apply32<2, MSTRESS_BF16>);
+    set(k_apply32<2, MSTRESS_BF16X3>);
     set(k_apply32<4, MSTRESS_TF32>);
     set(k_apply32<4, MSTRESS_BF16>);
     set(k_apply32<4, MSTRESS_BF16X3>);
@@ -685,15 +486,17 @@ void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool
     ApplyArgs a = apply_args(s, x, z, st, Y, false);
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
     if (m <= 80) {
-        size_t smem = (size_t)ns * (m * kTile64 + 80 * m) * sizeof(float);
-        if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<10, MSTRESS_TF32>, s, smem, a);
-        else if (prec == MSTRESS_BF16) launch_with_smem(k_apply32<10, MSTRESS_BF16>, s, smem, a);
-        else launch_with_smem(k_apply32<10, MSTRESS_BF16X3>, s, smem, a);
+        const size_t smem = (size_t)ns * (m * kTile64 + 16 * m) * sizeof(float);
+        const int panels = (m + 15) / 16;
+        if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<2, MSTRESS_TF32>, s, smem, a, panels);
+        else if (prec == MSTRESS_BF16) launch_with_smem(k_apply32<2, MSTRESS_BF16>, s, smem, a, panels);
+        else launch_with_smem(k_apply32<2, MSTRESS_BF16X3>, s, smem, a, panels);
     } else {
-        size_t smem = (size_t)ns * (m * kTile64 + 32 * m) * sizeof(float);
-        if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<4, MSTRESS_TF32>, s, smem, a);
-        else if (prec == MSTRESS_BF16) launch_with_smem(k_apply32<4, MSTRESS_BF16>, s, smem, a);
-        else launch_with_smem(k_apply32<4, MSTRESS_BF16X3>, s, smem, a);
+        const size_t smem = (size_t)ns * (m * kTile64 + 32 * m) * sizeof(float);
+        const int panels = (m + 31) / 32;
+        if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<4, MSTRESS_TF32>, s, smem, a, panels);
+        else if (prec == MSTRESS_BF16) launch_with_smem(k_apply32<4, MSTRESS_BF16>, s, smem, a, panels);
+        else launch_with_smem(k_apply32<4, MSTRESS_BF16X3>, s, smem, a, panels);
     }
 }
 
@@ -903,13 +706,20 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
 
     std::vector<BlockRef> bref;
     std::vector<VecWork> vwork;
-    std::vector<ApplyWork> awork, awork_tc;
+    std::vector<ApplyWork> awork, awork_tc, awork_rec;
     std::vector<int> blist;
     std::vector<uint8_t> fixed;
     std::vector<double> xbc;
     bool any_presc = false;
-    for (auto& li : in)
+    int64_t total_blocks = 0;
+    for (auto& li : in) {
         if (li.bc && li.bc->n_prescribed) any_presc = true;
+        total_blocks += (int64_t)li.L->nx * li.L->ny;
+    }
+    // tensor-core apply tiles: the largest of 128 / 64 / 32 blocks that still
+    // gives every SM two tiles (the tile's gather, not its MMA, sets the time)
+    s->tc_tile = kTileTC;
+    while (s->tc_tile > 32 && total_blocks < (int64_t)s->tc_tile * 2 * ctx->num_sms) s->tc_tile /= 2;
     int64_t vec_off = 0, block_off = 0;
     for (int a = 0; a < s->n_arrays; ++a) {
         const mstress_layout* L = in[a].L;
@@ -941,16 +751,20 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
                 s->site.push_back((uint8_t)t);
                 per_type[t].push_back((int)e);
             }
-        // tiles of one type and one array: 32 blocks (CUDA-core kernels) and
-        // kTileTC blocks (tensor-core kernels) over the same block list
+        // tiles of one type and one array over the same block list: 32 blocks
+        // (CUDA-core kernels), tc_tile blocks (tensor-core apply) and 128
+        // blocks (tensor-core recovery)
         for (int t = 0; t < s->n_types; ++t) {
             auto& v = per_type[t];
             const int start = (int)blist.size();
             for (int e : v) blist.push_back(e);
-            for (size_t st = 0; st < v.size(); st += kTile64)
-                awork.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(kTile64, v.size() - st)});
-            for (size_t st = 0; st < v.size(); st += kTileTC)
-                awork_tc.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(kTileTC, v.size() - st)});
+            auto tiles = [&](std::vector<ApplyWork>& out, size_t tile) {
+                for (size_t st = 0; st < v.size(); st += tile)
+                    out.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(tile, v.size() - st)});
+            };
+            tiles(awork, kTile64);
+            tiles(awork_tc, (size_t)s->tc_tile);
+            tiles(awork_rec, kTileTC);
         }
         if (any_presc) {
             fixed.resize(vec_off + A.n_dof, 0);
@@ -975,6 +789,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     s->n_vwork = (int)vwork.size();
     s->n_awork = (int)awork.size();
     s->n_awork_tc = (int)awork_tc.size();
+    s->n_awork_rec = (int)awork_rec.size();
 
     cudaStream_t st = ctx->stream;
     auto up = [&](DBuf& d, const void* src, size_t bytes) {
@@ -987,6 +802,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     up(s->d_blist, blist.data(), blist.size() * sizeof(int));
     up(s->d_awork, awork.data(), awork.size() * sizeof(ApplyWork));
     up(s->d_awork_tc, awork_tc.data(), awork_tc.size() * sizeof(ApplyWork));
+    up(s->d_awork_rec, awork_rec.data(), awork_rec.size() * sizeof(ApplyWork));
     up(s->d_vwork, vwork.data(), vwork.size() * sizeof(VecWork));
     up(s->d_site, s->site.data(), s->site.size());
     if (any_presc) {

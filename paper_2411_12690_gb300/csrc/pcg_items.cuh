@@ -95,26 +95,66 @@ __device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __r
 // Interface sum of one vector work item: q_g = sum of Y_e over the owning
 // blocks (fixed order), p updated to z + beta p when z is given; returns this
 // thread's share of <p, q>.
+// Each thread handles kIsumU DOFs at once and issues all their loads (mask,
+// direction, up to four owner contributions) before combining, so a work item
+// costs one round trip to L2 instead of a chain of dependent ones. The owner
+// candidates are visited rows ascending then columns ascending, as in
+// for_owners; constrained rows are zeroed after the sum.
+constexpr int kIsumU = 4;
+
 template <class V, class YT>
 __device__ __forceinline__ double isum_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm, const double* dinv,
                                             int ldY, const YT* __restrict__ Y, V* __restrict__ p,
                                             const V* __restrict__ z, V* __restrict__ q, double beta) {
+    const int n = lm->n, n1 = n - 1;
+    const int16_t* __restrict__ surf = lm->surf_idx;
+    const long long end = it.start + it.count;
     double acc = 0;
-    for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += blockDim.x) {
-        double s = 0;
-        if (!dinv || dinv[g] != 0.0) {
-            int comp, gx, gy, gz;
-            lattice_coords(A, g, comp, gx, gy, gz);
-            for_owners(A, lm->surf_idx, lm->n, gx, gy, gz,
-                       [&](long long blk, int sidx) { s += (double)Y[blk * ldY + 3 * sidx + comp]; });
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * kIsumU) {
+        double s[kIsumU], dv[kIsumU];
+        V pv[kIsumU], zv[kIsumU];
+#pragma unroll
+        for (int u = 0; u < kIsumU; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            s[u] = 0;
+            dv[u] = 0;
+            pv[u] = V(0);
+            zv[u] = V(0);
+            if (g < end) {
+                dv[u] = dinv ? dinv[g] : 1.0;
+                pv[u] = p[g];
+                if (z) zv[u] = z[g];
+                int comp, gx, gy, gz;
+                lattice_coords(A, g, comp, gx, gy, gz);
+                const int ih0 = gx / n1, jh0 = gy / n1;
+                const int ih = min(ih0, A.nx - 1), jh = min(jh0, A.ny - 1);
+                const int il = max((gx % n1 == 0) ? ih0 - 1 : ih0, 0), jl = max((gy % n1 == 0) ? jh0 - 1 : jh0, 0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = (c >> 1) ? jh : jl, i = (c & 1) ? ih : il;
+                    const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
+                    if (use) {
+                        const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
+                        if (sidx >= 0)
+                            s[u] += (double)Y[(A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp];
+                    }
+                }
+            }
         }
-        V pv = p[g];
-        if (z) {
-            pv = p_next(z[g], pv, beta);
-            p[g] = pv;
+#pragma unroll
+        for (int u = 0; u < kIsumU; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                const double sv = dv[u] != 0.0 ? s[u] : 0.0;
+                V pn = pv[u];
+                if (z) {
+                    pn = p_next(zv[u], pv[u], beta);
+                    p[g] = pn;
+                }
+                q[g] = (V)sv;
+                acc += (double)pn * sv;
+            }
         }
-        q[g] = (V)s;
-        acc += (double)pv * s;
     }
     return acc;
 }
@@ -126,15 +166,33 @@ __device__ __forceinline__ void vec1_item(const VecWork& it, const double* dinv,
                                           const V* p, const V* q, double& srz, double& srr) {
     srz = 0;
     srr = 0;
-    for (long long g = it.start + threadIdx.x; g < it.start + it.count; g += blockDim.x) {
-        double pv = (double)p[g], qv = (double)q[g];
-        x[g] = (V)((double)x[g] + al * pv);
-        V rv = (V)((double)r[g] - al * qv);
-        V zv = (V)(dinv[g] * (double)rv);
-        r[g] = rv;
-        z[g] = zv;
-        srz += (double)rv * (double)zv;
-        srr += (double)rv * (double)rv;
+    const long long end = it.start + it.count;
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * kIsumU) {
+        double pv[kIsumU], qv[kIsumU], xv[kIsumU], rv0[kIsumU], dv[kIsumU];
+#pragma unroll
+        for (int u = 0; u < kIsumU; ++u) {   // all loads first
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                pv[u] = (double)p[g];
+                qv[u] = (double)q[g];
+                xv[u] = (double)x[g];
+                rv0[u] = (double)r[g];
+                dv[u] = dinv[g];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kIsumU; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                x[g] = (V)(xv[u] + al * pv[u]);
+                const V rv = (V)(rv0[u] - al * qv[u]);
+                const V zv = (V)(dv[u] * (double)rv);
+                r[g] = rv;
+                z[g] = zv;
+                srz += (double)rv * (double)zv;
+                srr += (double)rv * (double)rv;
+            }
+        }
     }
 }
 

@@ -6,7 +6,7 @@
 
 namespace ms {
 
-constexpr int kVecChunk = 512;    // lattice DOFs per vector work item (2 per thread)
+constexpr int kVecChunk = 1024;   // lattice DOFs per vector work item (4 per thread of 256)
 constexpr int kTile64 = 32;       // blocks per CUDA-core apply / recovery tile
 constexpr int kTileTC = 128;      // blocks per tensor-core apply tile (the MMA M dimension)
 
@@ -75,8 +75,10 @@ struct mstress_sol_s {
     std::vector<ms::ArrayDev> arrays;
     std::vector<mstress_block> types;     // not owned
     std::vector<uint8_t> site;            // type per block (global block order)
-    ms::DBuf d_lm, d_arrays, d_bref, d_blist, d_awork, d_awork_tc, d_vwork, d_site;
-    int n_awork = 0, n_awork_tc = 0, n_vwork = 0;
+    ms::DBuf d_lm, d_arrays, d_bref, d_blist, d_awork, d_awork_tc, d_awork_rec, d_vwork, d_site;
+    int n_awork = 0, n_awork_tc = 0, n_awork_rec = 0, n_vwork = 0;
+    int tc_tile = 128;                    // blocks per tensor-core apply tile (<= 128; smaller tiles
+                                          // spread a small array's gather over more SMs)
     ms::DBuf b, dinv, fixed;              // FP64 right-hand side, Jacobi inverse (0 on constrained DOFs)
     ms::DBuf xbc;                         // prescribed values (lifting), or empty
     ms::PcgVectors v64, v32;              // FP64 outer / plain vectors, FP32 inner vectors

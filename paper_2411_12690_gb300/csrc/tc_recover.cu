@@ -239,15 +239,17 @@ void recover_vm_tc(mstress_sol_s* s, float* out) {
         configured = true;
     }
     DBuf cimg;
-    alloc_into(ctx, cimg, (size_t)s->n_awork_tc * sh.ns * sh.plane, true);
+    alloc_into(ctx, cimg, (size_t)s->n_awork_rec * sh.ns * sh.plane, true);
     ApplyArgs aa = apply_args(s, s->v64.x.ptr, nullptr, nullptr, nullptr, true);
-    k_coeff_image<<<std::max(1, std::min(s->n_awork_tc, ctx->num_sms * 8)), 256, 0, ctx->stream>>>(
+    aa.work = s->d_awork_rec.as<ApplyWork>();   // 128-block tiles
+    aa.n_work = s->n_awork_rec;
+    k_coeff_image<<<std::max(1, std::min(s->n_awork_rec, ctx->num_sms * 8)), 256, 0, ctx->stream>>>(
         aa, sh, prec, cimg.as<uint8_t>());
     MS_LAUNCH_CHECK();
     RecTcArgs ra;
     std::memset(&ra, 0, sizeof(ra));
-    ra.work = s->d_awork_tc.as<ApplyWork>();
-    ra.n_work = s->n_awork_tc;
+    ra.work = s->d_awork_rec.as<ApplyWork>();
+    ra.n_work = s->n_awork_rec;
     ra.blist = s->d_blist.as<int>();
     ra.cimg = cimg.as<uint8_t>();
     for (int t = 0; t < s->n_types; ++t) {
@@ -258,7 +260,7 @@ void recover_vm_tc(mstress_sol_s* s, float* out) {
     ra.out = out;
     ra.err = s->flag.as<int>() + 2;
     const int chunks = (sh.n_etiles + kTilesPerItem - 1) / kTilesPerItem;
-    const int items = s->n_awork_tc * chunks;
+    const int items = s->n_awork_rec * chunks;
     const int per_sm = sh.smem > 100 * 1024 ? 1 : 2;
     const int grid = std::max(1, std::min(items, ctx->num_sms * per_sm));
     switch (prec) {
