@@ -247,6 +247,26 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
 int mstress_apply(mstress_ctx ctx, const mstress_layout* layout, const double* x_dev,
                   double* y_dev, int precision);
 
+/* Operator apply that allocates no memory (the paper has no counterpart; this
+   is a service for callers that cannot allocate device memory when they need
+   the operator: code inside a CUDA stream capture they do not own, loops whose
+   memory is fixed up front, hosts whose allocator belongs to another runtime).
+   Computes y = A_global x in FP64 for an nx*ny array whose sites all use the
+   block model blk, with x and y device vectors on the lattice of that array
+   (X*Y*Z*3 doubles, as in mstress_apply; constrained DOFs are not masked).
+   Work is issued on cuda_stream (a cudaStream_t; NULL = legacy stream) and is
+   not waited for. The only scratch, the element products, lives in a fixed
+   32 MiB device array inside the library that every GPU loading the library
+   holds until the process exits: nx*ny*round_up(m,16)*8 bytes must fit (e.g.
+   at most 52428 blocks at m = 78, 13797 at m = 294), else MSTRESS_EINVAL.
+   The first call on a device looks up that array's address (and must come
+   before any stream capture); later calls make no set-up call. Every call
+   shares the array and leaves its contents behind (nothing in it needs to
+   start at zero); calls whose work may overlap on the GPU race on it and must
+   be serialised by the caller. */
+int mstress_apply_noalloc(mstress_block blk, int nx, int ny, const double* x_dev, double* y_dev,
+                          void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,7 @@ SIGNATURES = {
     "mstress_apply": (I, [P, C.POINTER(mstress_layout), P, P, I]),
     "mstress_launch_count": (I, [C.POINTER(C.c_int64)]),
     "mstress_profile": (I, [P, P, I, I, PD]),
+    "mstress_apply_noalloc": (I, [P, I, I, P, P, P]),
 }
 
 _lib = None
