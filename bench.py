@@ -251,41 +251,51 @@ def ours(args):
         dist.all_reduce(et, op=dist.ReduceOp.MAX)
     e2e_value = world * n_blocks * args.steps / float(et.item())
 
-    # roofline of the dominant kernel, timed live with CUDA events on the context stream
+    # roofline of the dominant kernel. The PCG runs as one persistent kernel
+    # whose phases are timed on the device (globaltimer at its grid barriers);
+    # the recovery kernel is timed with CUDA events on the context stream.
     sol = step(vm_dev)
     info = sol.info()
-    t_apply = api.profile(ctx, sol, 0, 20)
-    t_isum = api.profile(ctx, sol, 1, 20)
+    ph = sol.phase_ms()
     t_rec = api.profile(ctx, sol, 3, 5)
-    n_iter = info["iters"]
-    share = {"apply": t_apply * n_iter, "isum": t_isum * n_iter, "recover": t_rec}
+    n_iter = max(1, ph["iterations"])
     m = 78
+    lat_dofs = 3 * (2 * nx + 1) * (2 * ny + 1) * 3          # lattice DOFs of the 100x100 array (n = 3)
     apply_flops = 2.0 * m * m * n_blocks * (3 if prec == 3 else 1)
     rec_flops = 2.0 * 6 * n_el * (m + 1) * n_blocks * (3 if prec == 3 else 1)
+    w = 8 if prec == 0 else 4
+    # algorithmic bytes of one PCG iteration: gather p, z per element DOF and
+    # write Y; read Y, p, z, D^-1 and write p, q; read p, q, x, r, D^-1 and write x, r, z
+    it_bytes = (2 * w * m * n_blocks + w * 80 * n_blocks) + (w * m * n_blocks + lat_dofs * (2 * w + 8 + 2 * w)) \
+        + lat_dofs * (4 * w + 8 + 3 * w)
+    sm_mhz = clk.get("sm_mhz") or 1900.0
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    sm_mhz = clk.get("sm_mhz") or 1900.0
+    hbm = peaks.get("hbm_gbs")
+    t_pcg = (ph["apply"] + ph["isum"] + ph["update"]) / n_iter        # ms per iteration
+    share = {"pcg": ph["apply"] + ph["isum"] + ph["update"], "recover": t_rec}
     if prec == 0:
         # FP64 pipe: 152 SMs x 2 DFMA/clk (4 flop/clk) at the sampled SM clock
         fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
-        dom = max(share, key=share.get) if share["recover"] > share["apply"] else "apply"
-        if dom == "recover":
-            roof = {"bound": "alu", "achieved": rec_flops / (t_rec * 1e-3) / 1e12, "peak": fp64_peak,
-                    "unit": "TFLOP/s", "traffic": None, "kernel": "k_recover<FP64> (von Mises epilogue)"}
-        else:
-            roof = {"bound": "alu", "achieved": apply_flops / (t_apply * 1e-3) / 1e12, "peak": fp64_peak,
-                    "unit": "TFLOP/s", "traffic": None, "kernel": "k_apply64 (element products, FP64)"}
-        roof["peak_source"] = "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock"
+        roof = {"bound": "alu", "achieved": apply_flops / (ph["apply"] / n_iter * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "traffic": None,
+                "kernel": "k_pcg<FP64> phase A (element products on the FP64 pipe)",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock (probe measured 1.257 TFLOP/s)"}
     else:
-        roof = {"bound": "alu", "achieved": apply_flops / (t_apply * 1e-3) / 1e12,
-                "peak": 152 * 256 * sm_mhz * 1e6 / 1e12, "unit": "TFLOP/s", "traffic": None,
-                "kernel": "k_apply32 (element products, reduced precision on CUDA cores)",
-                "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x sampled SM clock"}
+        roof = {"bound": "hbm", "achieved": it_bytes / (t_pcg * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "traffic": None, "kernel": "k_pcg<tensor-core> (persistent PCG iteration: apply + interface sum + update)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800 GB/s"}
+        if not hbm:
+            roof["peak"] = 6800.0
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["avg_launch_ms"] = {"apply": t_apply, "isum": t_isum, "recover": t_rec}
+    roof["per_iteration_ms"] = {"apply": ph["apply"] / n_iter, "isum": ph["isum"] / n_iter,
+                                "update": ph["update"] / n_iter}
+    roof["recover_ms"] = t_rec
+    roof["recover_tflops"] = rec_flops / (t_rec * 1e-3) / 1e12
+    roof["time_share"] = {k: v / sum(share.values()) for k, v in share.items()}
     sol.close()
 
     if rank == 0:

@@ -240,6 +240,12 @@ int mstress_launch_count(int64_t* n);
      phase 3  von Mises recovery (contraction + epilogue) into scratch */
 int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, double* avg_ms);
 
+/* Time spent inside the persistent solver's iterations of this solution,
+   measured on the device at its grid barriers: ms4[0..2] = milliseconds in
+   the element products, the interface sum and the vector update (summed over
+   all iterations and refinement steps), ms4[3] = number of iterations. */
+int mstress_sol_phase_ms(mstress_sol sol, double* ms4);
+
 /* Apply the assembled reduced operator of a layout in FP64 (one matrix-free
    K_r apply plus interface sum, the kernel pair of every PCG iteration):
    y = A_global x on the lattice vector (X*Y*Z*3 doubles, device pointers).

@@ -104,6 +104,7 @@ SIGNATURES = {
     "mstress_launch_count": (I, [C.POINTER(C.c_int64)]),
     "mstress_profile": (I, [P, P, I, I, PD]),
     "mstress_apply_noalloc": (I, [P, I, I, P, P, P]),
+    "mstress_sol_phase_ms": (I, [P, PD]),
 }
 
 _lib = None

@@ -232,6 +232,13 @@ class Solution:
                                                       C.byref(st)))
         return dict(iters=it.value, outer=outer.value, rel_res=rr.value, status=st.value)
 
+    def phase_ms(self):
+        """Device time in the persistent solver's phases (element products,
+        interface sum, vector update), summed over iterations, and the count."""
+        v = (C.c_double * 4)()
+        self.ctx._check(self.ctx.lib.mstress_sol_phase_ms(self.h, v))
+        return dict(apply=v[0], isum=v[1], update=v[2], iterations=int(v[3]))
+
     def recover_size(self, what: int) -> int:
         n = C.c_size_t()
         self.ctx._check(self.ctx.lib.mstress_recover_size(self.h, what, C.byref(n)))

@@ -825,6 +825,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     alloc_into(ctx, s->part, 3 * (size_t)s->n_vwork * sizeof(double));
     alloc_into(ctx, s->flag, 64);
     alloc_into(ctx, s->tickets, 2 * (size_t)s->n_arrays * sizeof(int));
+    alloc_into(ctx, s->timers, 4 * sizeof(unsigned long long));
     const bool mixed = s->precision != MSTRESS_FP64;
     alloc_into(ctx, s->Y, (size_t)s->n_blocks * s->ldY * (mixed ? sizeof(float) : sizeof(double)), false);
     if (mixed) {
@@ -1093,6 +1094,16 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
     *avg_ms = ms / reps;
     check_device_error(s);
     MS_API_END(ctx)
+}
+
+int mstress_sol_phase_ms(mstress_sol sol, double* ms4) {
+    if (!sol || !ms4) return MSTRESS_EINVAL;
+    MS_API_BEGIN
+    unsigned long long t[4] = {0, 0, 0, 0};
+    MS_CUDA(cudaMemcpy(t, sol->timers.ptr, sizeof(t), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) ms4[k] = t[k] * 1e-6;
+    ms4[3] = (double)t[3];
+    MS_API_END(sol->ctx)
 }
 
 int mstress_recover_size(mstress_sol sol, int what, size_t* bytes) {

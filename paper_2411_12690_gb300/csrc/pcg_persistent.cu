@@ -43,7 +43,24 @@ struct PcgArgs {
     int* err;                  // 1: tensor-core wait expired, 2: grid barrier expired
     int* abort;
     int max_loops;
+    unsigned long long* timers;   // optional: ns spent in phases A, B, C and the loop count
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// CTA 0 accumulates the wall time of a phase (from its start to the end of
+// the grid barrier that closes it) into timers[phase].
+__device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned long long& t_prev) {
+    if (a.timers && blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long t = global_ns();
+        a.timers[phase] += t - t_prev;
+        t_prev = t;
+    }
+}
 
 // Grid-wide barrier with a bounded wait. Returns false (in every thread of the
 // CTA) when the grid is aborting or the wait expired.
@@ -113,6 +130,7 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
     V* z = static_cast<V*>(a.z);
     V* p = static_cast<V*>(a.p);
     V* q = static_cast<V*>(a.q);
+    unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
         bool failed = false;
@@ -142,6 +160,7 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
             atomicExch(a.abort, 1);
         }
         if (!grid_sync(a, &s_ok)) break;
+        phase_mark(a, 0, t_prev);
         // ---- phase B: interface sum, <p, q>, alpha
         for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
             const VecWork it = a.vwork[w];
@@ -176,6 +195,7 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
             __syncthreads();
         }
         if (!grid_sync(a, &s_ok)) break;
+        phase_mark(a, 1, t_prev);
         // ---- phase C: vector update, <r,z>, <r,r>, beta, stopping test
         for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
             const VecWork it = a.vwork[w];
@@ -218,6 +238,8 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
             __syncthreads();
         }
         if (!grid_sync(a, &s_ok)) break;
+        phase_mark(a, 2, t_prev);
+        if (a.timers && blockIdx.x == 0 && tid == 0) a.timers[3] += 1;
         if (*(volatile int*)a.n_active <= 0) break;
     }
     if (AM == AM_TC) {
@@ -276,6 +298,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     a.bar = reinterpret_cast<unsigned*>(flag + 5);
     a.abort = flag + 7;
     a.max_loops = max_iter + 1;
+    a.timers = s->timers.as<unsigned long long>();
     MS_CUDA(cudaMemsetAsync(flag + 5, 0, 3 * sizeof(int), s->ctx->stream));
     MS_CUDA(cudaMemsetAsync(s->tickets.ptr, 0, s->tickets.bytes, s->ctx->stream));
     const int m = s->m;

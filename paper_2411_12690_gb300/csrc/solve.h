@@ -87,6 +87,7 @@ struct mstress_sol_s {
     ms::DBuf flag;                        // device ints: [0] any active, [1] CTA ticket, [2] error,
                                           // [3] loop count, [4] arrays active, [5..6] grid barrier, [7] abort
     ms::DBuf tickets;                     // 2 ints per array (persistent solver folds)
+    ms::DBuf timers;                      // 4 u64: ns in phases A, B, C of the persistent solver, loops
     ms::TypeTab tt{};
     std::vector<ms::ArrayResult> results;
     // CUDA graphs of the iteration loop (conditional WHILE node), by vector precision
