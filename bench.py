@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=list(PREC))
     ap.add_argument("--nx", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="array100", choices=["array100", "batch256", "serve"],
+                    help="array100: the headline 100x100 array; batch256: 256 uneven arrays in one batched "
+                         "solve; serve: a Poisson request stream through the continuous-batching server")
+    ap.add_argument("--n-arrays", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--load", type=float, default=0.8, help="serve: arrival rate as a fraction of capacity")
     return ap.parse_args()
 
 
@@ -321,10 +327,120 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def _variant_models(ctx, W):
+    """Both pitch variants (15 and 20 um, 24x24x20 mesh, degree 4) with their dummy blocks."""
+    return [[ctx.build_block(v), ctx.build_block(v.dummy())] for v in (W.BLOCK_P15, W.BLOCK_P20)]
+
+
+def batch_bench(args):
+    """256 independent arrays (side log-uniform 4..64, occupancy U[0.5,1],
+    pitch 15/20 um, dT U[-300,-150] K) solved and recovered in one batch."""
+    import torch
+
+    from paper_2411_12690_gb300 import _lib as L
+    from paper_2411_12690_gb300 import api
+    from paper_2411_12690_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(stream=stream.cuda_stream, precision=PREC[args.precision])
+    models = _variant_models(ctx, W)
+    jobs = W.batch_arrays(args.n_arrays, seed=0)
+    spec = [dict(site_type=j.site_type, blocks=models[j.pitch], dT=j.dT) for j in jobs]
+    n_blocks = sum(j.site_type.size for j in jobs)
+    n_el = W.BLOCK_P15.ex * W.BLOCK_P15.ey * W.BLOCK_P15.ez
+    vm = torch.empty(n_blocks * n_el, dtype=torch.float64 if PREC[args.precision] == 0 else torch.float32,
+                     device="cuda")
+    times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol = ctx.solve_batch(spec)
+        sol.recover(L.MSTRESS_VM_ELEM, out=vm)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+        infos = [sol.info(a) for a in range(len(jobs))]
+        sol.close()
+    total = sum(times)
+    print(json.dumps({"metric": "TSV blocks solved+recovered/s (256-array batch)", "value": n_blocks * len(times) / total,
+                      "unit": "blocks/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "dtype": DTYPE[args.precision],
+                      "data": "synthetic", "config": {
+                          "workload": f"{len(jobs)} arrays, side log-uniform 4..64, occupancy U[0.5,1], pitch 15/20 um "
+                                      f"(24x24x20 mesh, degree-4 basis, m=294), dT U[-300,-150] K, one batched solve",
+                          "blocks": n_blocks, "max_pcg_iters": max(i["iters"] for i in infos),
+                          "max_refinement_steps": max(i["outer"] for i in infos),
+                          "max_rel_res": max(i["rel_res"] for i in infos)}}), flush=True)
+
+
+def serve_bench(args):
+    """Poisson request stream through the continuous-batching server: arrays
+    log-uniform 2..128, occupancy U[0.5,1], pitch 15/20 um, dT U[-300,-150] K;
+    arrival rate = load x the capacity measured by a closed-loop pass."""
+    import torch
+
+    from paper_2411_12690_gb300 import api
+    from paper_2411_12690_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(stream=stream.cuda_stream, precision=PREC[args.precision])
+    models = _variant_models(ctx, W)
+
+    def run(reqs, rate_scale):
+        srv = api.Server(ctx, max_slots=64)
+        t0 = time.perf_counter()
+        pending = list(reqs)
+        done, lat, blocks = 0, [], 0
+        ids = {}
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while pending and pending[0].t_arrival * rate_scale <= now:
+                r = pending.pop(0)
+                ids[srv.submit(r.job.site_type, models[r.job.pitch], r.job.dT)] = r
+            q, running, _ = srv.step()
+            while True:
+                rid = srv.poll()
+                if not rid:
+                    break
+                inf = srv.info(rid)
+                lat.append(inf["latency_ms"])
+                blocks += ids[rid].job.site_type.size
+                srv.release(rid)
+                done += 1
+            if not running and not q and pending:
+                time.sleep(max(0.0, min(0.01, pending[0].t_arrival * rate_scale - (time.perf_counter() - t0))))
+        elapsed = time.perf_counter() - t0
+        srv.close()
+        return blocks / elapsed, lat, elapsed
+
+    warm = W.request_stream(1.0, 8, seed=1)
+    run([W.Request(0.0, r.job) for r in warm], 0.0)                       # warm-up
+    probe = W.request_stream(1.0, max(16, args.requests // 4), seed=2)
+    cap_blocks, _, cap_t = run([W.Request(0.0, r.job) for r in probe], 0.0)  # closed loop: capacity
+    cap_rps = len(probe) / cap_t
+    reqs = W.request_stream(args.load * cap_rps, args.requests, seed=0)
+    thr, lat, elapsed = run(reqs, 1.0)
+    lat = sorted(lat)
+    print(json.dumps({"metric": "served TSV blocks/s with p50/p99 request latency", "value": thr, "unit": "blocks/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE[args.precision], "data": "synthetic",
+                      "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                      "requests": len(lat), "elapsed_s": elapsed,
+                      "config": {"workload": "Poisson stream, arrays log-uniform 2..128, occupancy U[0.5,1], pitch "
+                                             "15/20 um (m=294), dT U[-300,-150] K, max 64 slots",
+                                 "arrival_rate_per_s": args.load * cap_rps, "load": args.load,
+                                 "closed_loop_capacity_blocks_per_s": cap_blocks}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batch256":
+        batch_bench(args)
+    elif args.workload == "serve":
+        serve_bench(args)
     else:
         ours(args)
 

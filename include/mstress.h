@@ -227,6 +227,48 @@ int mstress_sol_info(mstress_sol sol, int array, int* iters, int* outer,
 int mstress_sol_count(mstress_sol sol, int* n_arrays, int64_t* n_blocks);
 void mstress_free_sol(mstress_sol sol);
 
+/* ------------------------------------------------------------ serving
+ * Continuous batching of global-stage queries (not in the paper: a serving
+ * layer over the global stage of section 4.3). A server owns a queue of
+ * requests -- one array each (layout against resident block models, dT,
+ * clamped faces) -- and solves every running request together as one batch by
+ * FP64-residual iterative refinement (a step = one FP64 residual check for
+ * every running array + one inner solve of the correction in the context's
+ * precision). Between steps: arrays whose check stopped them retire (their
+ * per-element von Mises field is recovered into the request), queued requests
+ * are admitted in arrival order while at most max_slots run and the estimated
+ * device footprint of running requests plus held results fits hbm_budget
+ * (0 = unlimited), and the batch is rebuilt with every continuing array's
+ * iterate. A request's arithmetic does not depend on the others, so its result
+ * is the same alone and in the mix. Requests must share basis order and block
+ * mesh size; prescribed displacements are not taken. Not thread safe. */
+typedef struct mstress_server_s* mstress_server;
+#define MSTRESS_RQ_QUEUED  0
+#define MSTRESS_RQ_RUNNING 1
+#define MSTRESS_RQ_DONE    2
+#define MSTRESS_RQ_FAILED  3
+int mstress_server_create(mstress_ctx ctx, int max_slots, size_t hbm_budget, mstress_server* out);
+/* Queue a request; *id receives its handle. The layout is copied. */
+int mstress_server_submit(mstress_server srv, const mstress_layout* layout, double dT, const mstress_bc* bc,
+                          int64_t* id);
+/* Admit, run one refinement step over the running batch, retire finished
+   requests. Returns the queue length, running count and requests finished. */
+int mstress_server_step(mstress_server srv, int* n_queued, int* n_running, int* n_finished);
+/* Next finished (or failed) request not yet polled, 0 if none. */
+int mstress_server_poll(mstress_server srv, int64_t* id);
+/* State (MSTRESS_RQ_*), inner PCG iterations, refinement steps, final relative
+   FP64 residual and latency from submit to retirement (ms, -1 while pending).
+   Returns the request's status (MSTRESS_OK, _ENOT_CONVERGED, _ENUMERIC, or
+   _ENOMEM if it can never fit the budget). */
+int mstress_server_info(mstress_server srv, int64_t id, int* state, int* iters, int* outer, double* rel_res,
+                        double* latency_ms);
+/* Copy a finished request's von Mises field ([block][n_el], FP64 in FP64
+   mode, else FP32) to dst (device if dst_on_device). */
+int mstress_server_result(mstress_server srv, int64_t id, void* dst, size_t dst_bytes, int dst_on_device);
+/* Forget a finished request and free its result. */
+int mstress_server_release(mstress_server srv, int64_t id);
+void mstress_free_server(mstress_server srv);
+
 /* Number of CUDA kernels this library has launched in this process (a graph
    replay counts its kernel nodes). For accounting in benchmarks. */
 int mstress_launch_count(int64_t* n);

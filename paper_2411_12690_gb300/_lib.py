@@ -105,6 +105,15 @@ SIGNATURES = {
     "mstress_profile": (I, [P, P, I, I, PD]),
     "mstress_apply_noalloc": (I, [P, I, I, P, P, P]),
     "mstress_sol_phase_ms": (I, [P, PD]),
+    "mstress_server_create": (I, [P, I, C.c_size_t, C.POINTER(P)]),
+    "mstress_server_submit": (I, [P, C.POINTER(mstress_layout), C.c_double, C.POINTER(mstress_bc),
+                                  C.POINTER(C.c_int64)]),
+    "mstress_server_step": (I, [P, PI, PI, PI]),
+    "mstress_server_poll": (I, [P, C.POINTER(C.c_int64)]),
+    "mstress_server_info": (I, [P, C.c_int64, PI, PI, PI, PD, PD]),
+    "mstress_server_result": (I, [P, C.c_int64, P, C.c_size_t, I]),
+    "mstress_server_release": (I, [P, C.c_int64]),
+    "mstress_free_server": (None, [P]),
 }
 
 _lib = None

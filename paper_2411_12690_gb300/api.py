@@ -266,6 +266,58 @@ class Solution:
         self.h = None
 
 
+class Server:
+    """Continuous-batching server over one context (mstress_server_*)."""
+
+    def __init__(self, ctx: Context, max_slots: int = 64, hbm_budget: int = 0):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._check(ctx.lib.mstress_server_create(ctx.h, max_slots, hbm_budget, C.byref(h)))
+        self.h = h
+
+    def submit(self, site_type, blocks, dT, clamp_bottom=True, clamp_top=False) -> int:
+        lay, keep = Context._layout(site_type, blocks)
+        bc, _ = Context._bc(clamp_bottom, clamp_top)
+        rid = C.c_int64()
+        self.ctx._check(self.ctx.lib.mstress_server_submit(self.h, C.byref(lay), float(dT), C.byref(bc),
+                                                           C.byref(rid)))
+        return rid.value
+
+    def step(self):
+        q, r, f = C.c_int(), C.c_int(), C.c_int()
+        self.ctx._check(self.ctx.lib.mstress_server_step(self.h, C.byref(q), C.byref(r), C.byref(f)))
+        return q.value, r.value, f.value
+
+    def poll(self) -> int:
+        rid = C.c_int64()
+        self.ctx._check(self.ctx.lib.mstress_server_poll(self.h, C.byref(rid)))
+        return rid.value
+
+    def info(self, rid: int):
+        st, it, outer = C.c_int(), C.c_int(), C.c_int()
+        rr, lat = C.c_double(), C.c_double()
+        rc = self.ctx.lib.mstress_server_info(self.h, rid, C.byref(st), C.byref(it), C.byref(outer), C.byref(rr),
+                                              C.byref(lat))
+        return dict(status=rc, state=st.value, iters=it.value, outer=outer.value, rel_res=rr.value,
+                    latency_ms=lat.value)
+
+    def result(self, rid: int, out):
+        if isinstance(out, np.ndarray):
+            ptr, dev, have = out.ctypes.data, 0, out.nbytes
+        else:
+            ptr, dev, have = out.data_ptr(), int(out.is_cuda), out.numel() * out.element_size()
+        self.ctx._check(self.ctx.lib.mstress_server_result(self.h, rid, C.c_void_p(ptr), have, dev))
+        return out
+
+    def release(self, rid: int):
+        self.ctx._check(self.ctx.lib.mstress_server_release(self.h, rid))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.mstress_free_server(self.h)
+            self.h = None
+
+
 def launch_count() -> int:
     """Kernels launched by libmstress in this process so far."""
     lib = L.load()

@@ -286,9 +286,10 @@ __global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ V
     }
 }
 
-// x64 += d32 for arrays still refining.
+// x64 += d (the inner solution) for arrays still refining.
+template <class D>
 __global__ void __launch_bounds__(kThreads) k_correct(const VecWork* vwork, int n_vwork, const PcgState* outer,
-                                                      double* x, const float* d) {
+                                                      double* x, const D* d) {
     for (int w = blockIdx.x; w < n_vwork; w += gridDim.x) {
         const VecWork it = vwork[w];
         if (!outer[it.array].active) continue;
@@ -651,13 +652,9 @@ bool outer_check(mstress_sol_s* s, void* Y64, int max_outer) {
     return s->ctx->h_flag[0] != 0;
 }
 
-// -------------------------------------------------------- solve set-up
-struct LayoutIn {
-    const mstress_layout* L;
-    double dT;
-    const mstress_bc* bc;
-};
+}  // namespace
 
+// -------------------------------------------------------- solve set-up
 void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     mstress_ctx ctx = s->ctx;
     for (auto& li : in) {
@@ -790,6 +787,8 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     s->n_awork = (int)awork.size();
     s->n_awork_tc = (int)awork_tc.size();
     s->n_awork_rec = (int)awork_rec.size();
+    s->h_awork = awork;
+    s->h_awork_rec = awork_rec;
 
     cudaStream_t st = ctx->stream;
     auto up = [&](DBuf& d, const void* src, size_t bytes) {
@@ -840,20 +839,27 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         alloc_into(ctx, s->v32.q, nv * sizeof(float), false);
         alloc_into(ctx, s->v32.state, s->n_arrays * sizeof(PcgState));
     }
+    if (s->inner64) {
+        alloc_into(ctx, s->v64i.x, nv * sizeof(double));
+        alloc_into(ctx, s->v64i.r, nv * sizeof(double), false);
+        alloc_into(ctx, s->v64i.z, nv * sizeof(double), false);
+        alloc_into(ctx, s->v64i.p, nv * sizeof(double), false);
+        alloc_into(ctx, s->v64i.q, nv * sizeof(double), false);
+        alloc_into(ctx, s->v64i.state, s->n_arrays * sizeof(PcgState));
+    }
 }
 
 void check_device_error(mstress_sol_s* s) {
     int f[4];
     MS_CUDA(cudaMemcpy(f, s->flag.ptr, sizeof(f), cudaMemcpyDeviceToHost));
-    MS_REQUIRE(f[2] == 0, MSTRESS_EDEVICE_TIMEOUT, "a tensor-core wait timed out on the device");
+    MS_REQUIRE(f[2] == 0, MSTRESS_EDEVICE_TIMEOUT, "a tensor-core wait or a grid barrier timed out on the device");
 }
 
-void run_solve(mstress_sol_s* s) {
+// a2: right-hand side and Jacobi diagonal, the FP64 element buffer of the
+// mixed modes, and the lifting of prescribed values (Eq. 13).
+void solve_prepare(mstress_sol_s* s) {
     mstress_ctx ctx = s->ctx;
     cudaStream_t stream = ctx->stream;
-    const mstress_opts& o = ctx->opts;
-    const bool mixed = s->precision != MSTRESS_FP64;
-    // a2: right-hand side and Jacobi diagonal
     RhsArgs ra;
     ra.vwork = s->d_vwork.as<VecWork>();
     ra.n_vwork = s->n_vwork;
@@ -867,72 +873,88 @@ void run_solve(mstress_sol_s* s) {
     ra.dinv = s->dinv.as<double>();
     k_rhs_diag<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(ra);
     MS_LAUNCH_CHECK();
-    DBuf Yfp64;   // FP64 element buffer for the FP64 operator in mixed modes
-    if (mixed) alloc_into(ctx, Yfp64, (size_t)s->n_blocks * s->ldY * sizeof(double), false);
-    void* Y64 = mixed ? Yfp64.ptr : s->Y.ptr;
-    if (s->xbc.ptr) {   // lifting (Eq. 13): b -= A x_bc on the free DOFs
-        launch_apply(s, MSTRESS_FP64, s->xbc.ptr, nullptr, false, nullptr, Y64);
-        launch_isum(s, Y64, false, s->xbc.ptr, nullptr, s->v64.q.ptr, false, nullptr, nullptr, nullptr);
+    if (s->precision != MSTRESS_FP64) {
+        alloc_into(ctx, s->Y64own, (size_t)s->n_blocks * s->ldY * sizeof(double), false);
+        s->Y64 = s->Y64own.ptr;
+    } else {
+        s->Y64 = s->Y.ptr;
+    }
+    if (s->xbc.ptr) {   // b -= A x_bc on the free DOFs
+        launch_apply(s, MSTRESS_FP64, s->xbc.ptr, nullptr, false, nullptr, s->Y64);
+        launch_isum(s, s->Y64, false, s->xbc.ptr, nullptr, s->v64.q.ptr, false, nullptr, nullptr, nullptr);
         k_lift_rhs<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->b.as<double>(),
                                                                             s->v64.q.as<double>(), s->dinv.as<double>());
         MS_LAUNCH_CHECK();
     }
-    if (!mixed) {
-        pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_iter, nullptr);
-        pcg_run<double>(s, s->v64, MSTRESS_FP64, o.max_iter);
+}
+
+// Outer (refinement) state from b: x = 0, ||b||, tolerance, step count 0.
+void refine_start(mstress_sol_s* s) {
+    const mstress_opts& o = s->ctx->opts;
+    pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_outer, nullptr);
+}
+
+// a5: FP64 residual and stopping test; true if any array takes another step.
+bool refine_check(mstress_sol_s* s) { return outer_check(s, s->Y64, s->ctx->opts.max_outer); }
+
+// One inner solve A d = r for every array still refining, in the inner
+// precision (FP32 vectors with the reduced-precision operator, or FP64 for
+// inner64), then x += d; inner iterations are added to the per-array counts.
+void refine_inner(mstress_sol_s* s) {
+    cudaStream_t stream = s->ctx->stream;
+    const mstress_opts& o = s->ctx->opts;
+    int used = 0;
+    for (auto& r : s->results) used = std::max(used, r.iters);
+    const int budget = std::max(1, o.max_iter - used);
+    const PcgState* gate = s->v64.state.as<PcgState>();
+    PcgVectors& vi = s->inner64 ? s->v64i : s->v32;
+    if (s->inner64) {
+        pcg_start<double>(s, vi, s->v64.r.as<double>(), o.inner_rtol, budget, gate);
+        pcg_run<double>(s, vi, MSTRESS_FP64, budget);
+        k_correct<double><<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
+            s->d_vwork.as<VecWork>(), s->n_vwork, gate, s->v64.x.as<double>(), vi.x.as<double>());
     } else {
-        // a5: FP64-residual iterative refinement around a reduced-precision PCG;
-        // the outer state counts refinement steps against max_outer
-        pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_outer, nullptr);
-        int inner_total = 0;
-        for (int k = 0; k <= o.max_outer; ++k) {
-            if (!outer_check(s, Y64, o.max_outer)) break;
-            const int budget = std::max(1, o.max_iter - inner_total);
-            pcg_start<float>(s, s->v32, s->v64.r.as<double>(), o.inner_rtol, budget, s->v64.state.as<PcgState>());
-            pcg_run<float>(s, s->v32, s->precision, budget);
-            k_correct<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
-                s->d_vwork.as<VecWork>(), s->n_vwork, s->v64.state.as<PcgState>(), s->v64.x.as<double>(),
-                s->v32.x.as<float>());
-            MS_LAUNCH_CHECK();
-            std::vector<PcgState> inner(s->n_arrays);
-            MS_CUDA(cudaMemcpyAsync(inner.data(), s->v32.state.ptr, inner.size() * sizeof(PcgState),
-                                    cudaMemcpyDeviceToHost, stream));
-            MS_CUDA(cudaStreamSynchronize(stream));
-            int mx = 0;
-            for (int a = 0; a < s->n_arrays; ++a) {
-                s->results[a].iters += inner[a].iters;
-                mx = std::max(mx, s->results[a].iters);
-            }
-            inner_total = mx;
-        }
+        pcg_start<float>(s, vi, s->v64.r.as<double>(), o.inner_rtol, budget, gate);
+        pcg_run<float>(s, vi, s->precision, budget);
+        k_correct<float><<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
+            s->d_vwork.as<VecWork>(), s->n_vwork, gate, s->v64.x.as<double>(), vi.x.as<float>());
     }
+    MS_LAUNCH_CHECK();
+    std::vector<PcgState> inner(s->n_arrays);
+    MS_CUDA(cudaMemcpyAsync(inner.data(), vi.state.ptr, inner.size() * sizeof(PcgState), cudaMemcpyDeviceToHost,
+                            stream));
+    MS_CUDA(cudaStreamSynchronize(stream));
+    for (int a = 0; a < s->n_arrays; ++a) s->results[a].iters += inner[a].iters;
+}
+
+// True FP64 residual of the final iterate, per-array results, and the
+// prescribed values added back to the solution.
+void solve_finish(mstress_sol_s* s, bool refined) {
+    cudaStream_t stream = s->ctx->stream;
     check_device_error(s);
-    // true FP64 residual of the final iterate (and the outer count)
-    {
-        std::vector<PcgState> before(s->n_arrays);
-        MS_CUDA(cudaMemcpyAsync(before.data(), s->v64.state.ptr, before.size() * sizeof(PcgState),
-                                cudaMemcpyDeviceToHost, stream));
-        launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, nullptr, false, nullptr, Y64);
-        launch_isum(s, Y64, false, s->v64.x.ptr, nullptr, s->v64.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
-        VecArgs va = vec_args(s, s->v64);
-        va.rhs = s->b.ptr;
-        va.r = s->v64.z.ptr;   // residual into z (scratch) so r keeps the recursive residual
-        k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
-        MS_LAUNCH_CHECK();
-        std::vector<double> prr(s->n_vwork);
-        MS_CUDA(cudaMemcpyAsync(prr.data(), va.part_rr, prr.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
-        MS_CUDA(cudaStreamSynchronize(stream));
-        for (int a = 0; a < s->n_arrays; ++a) {
-            const ArrayDev& A = s->arrays[a];
-            double rr = 0;
-            for (int w = 0; w < A.n_vwork; ++w) rr += prr[A.vwork_off + w];
-            ArrayResult& R = s->results[a];
-            R.rel_res = before[a].bb > 0 ? std::sqrt(rr / before[a].bb) : 0.0;
-            if (mixed) R.outer = before[a].iters;
-            else R.iters = before[a].iters;
-            R.status = before[a].status;
-            if (!std::isfinite(R.rel_res)) R.status = MSTRESS_ENUMERIC;
-        }
+    std::vector<PcgState> before(s->n_arrays);
+    MS_CUDA(cudaMemcpyAsync(before.data(), s->v64.state.ptr, before.size() * sizeof(PcgState), cudaMemcpyDeviceToHost,
+                            stream));
+    launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, nullptr, false, nullptr, s->Y64);
+    launch_isum(s, s->Y64, false, s->v64.x.ptr, nullptr, s->v64.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
+    VecArgs va = vec_args(s, s->v64);
+    va.rhs = s->b.ptr;
+    va.r = s->v64.z.ptr;   // residual into z (scratch) so r keeps the recursive residual
+    k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
+    MS_LAUNCH_CHECK();
+    std::vector<double> prr(s->n_vwork);
+    MS_CUDA(cudaMemcpyAsync(prr.data(), va.part_rr, prr.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(cudaStreamSynchronize(stream));
+    for (int a = 0; a < s->n_arrays; ++a) {
+        const ArrayDev& A = s->arrays[a];
+        double rr = 0;
+        for (int w = 0; w < A.n_vwork; ++w) rr += prr[A.vwork_off + w];
+        ArrayResult& R = s->results[a];
+        R.rel_res = before[a].bb > 0 ? std::sqrt(rr / before[a].bb) : 0.0;
+        if (refined) R.outer = before[a].iters;
+        else R.iters = before[a].iters;
+        R.status = before[a].status;
+        if (!std::isfinite(R.rel_res)) R.status = MSTRESS_ENUMERIC;
     }
     if (s->xbc.ptr) {
         k_add_bc<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->v64.x.as<double>(),
@@ -940,6 +962,25 @@ void run_solve(mstress_sol_s* s) {
         MS_LAUNCH_CHECK();
     }
     MS_CUDA(cudaStreamSynchronize(stream));
+}
+
+namespace {
+
+void run_solve(mstress_sol_s* s) {
+    const mstress_opts& o = s->ctx->opts;
+    solve_prepare(s);
+    if (s->precision == MSTRESS_FP64) {
+        pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_iter, nullptr);
+        pcg_run<double>(s, s->v64, MSTRESS_FP64, o.max_iter);
+        solve_finish(s, false);
+        return;
+    }
+    refine_start(s);
+    for (int k = 0; k <= o.max_outer; ++k) {
+        if (!refine_check(s)) break;
+        refine_inner(s);
+    }
+    solve_finish(s, true);
 }
 
 int solve_common(mstress_ctx ctx, const std::vector<LayoutIn>& in, mstress_sol* out) {

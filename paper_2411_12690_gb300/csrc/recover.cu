@@ -229,6 +229,44 @@ size_t recover_bytes(const mstress_sol_s* s, int what) {
     }
 }
 
+void recover_arrays(mstress_sol_s* s, int what, void* dst_dev, const std::vector<int>& arrays) {
+    std::vector<char> want(s->n_arrays, 0);
+    for (int a : arrays) want[a] = 1;
+    std::vector<ApplyWork> w, wr;
+    for (auto& it : s->h_awork)
+        if (want[it.array]) w.push_back(it);
+    for (auto& it : s->h_awork_rec)
+        if (want[it.array]) wr.push_back(it);
+    if (w.empty()) return;
+    DBuf dw, dwr;
+    alloc_into(s->ctx, dw, w.size() * sizeof(ApplyWork), false);
+    alloc_into(s->ctx, dwr, std::max<size_t>(1, wr.size()) * sizeof(ApplyWork), false);
+    MS_CUDA(cudaMemcpyAsync(dw.ptr, w.data(), w.size() * sizeof(ApplyWork), cudaMemcpyHostToDevice, s->ctx->stream));
+    if (!wr.empty())
+        MS_CUDA(cudaMemcpyAsync(dwr.ptr, wr.data(), wr.size() * sizeof(ApplyWork), cudaMemcpyHostToDevice,
+                                s->ctx->stream));
+    // run the ordinary recovery over the filtered tile lists
+    std::swap(s->d_awork, dw);
+    std::swap(s->d_awork_rec, dwr);
+    const int n0 = s->n_awork, n1 = s->n_awork_rec;
+    s->n_awork = (int)w.size();
+    s->n_awork_rec = (int)wr.size();
+    try {
+        recover(s, what, dst_dev, true);
+    } catch (...) {
+        std::swap(s->d_awork, dw);
+        std::swap(s->d_awork_rec, dwr);
+        s->n_awork = n0;
+        s->n_awork_rec = n1;
+        throw;
+    }
+    MS_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    std::swap(s->d_awork, dw);
+    std::swap(s->d_awork_rec, dwr);
+    s->n_awork = n0;
+    s->n_awork_rec = n1;
+}
+
 void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev) {
     mstress_ctx ctx = s->ctx;
     cudaStream_t st = ctx->stream;

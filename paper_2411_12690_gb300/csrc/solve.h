@@ -77,11 +77,16 @@ struct mstress_sol_s {
     std::vector<uint8_t> site;            // type per block (global block order)
     ms::DBuf d_lm, d_arrays, d_bref, d_blist, d_awork, d_awork_tc, d_awork_rec, d_vwork, d_site;
     int n_awork = 0, n_awork_tc = 0, n_awork_rec = 0, n_vwork = 0;
+    std::vector<ms::ApplyWork> h_awork, h_awork_rec;   // host copies (filtered recovery)
     int tc_tile = 128;                    // blocks per tensor-core apply tile (<= 128; smaller tiles
                                           // spread a small array's gather over more SMs)
     ms::DBuf b, dinv, fixed;              // FP64 right-hand side, Jacobi inverse (0 on constrained DOFs)
     ms::DBuf xbc;                         // prescribed values (lifting), or empty
     ms::PcgVectors v64, v32;              // FP64 outer / plain vectors, FP32 inner vectors
+    ms::PcgVectors v64i;                  // FP64 inner vectors (refinement with an FP64 inner solve)
+    bool inner64 = false;                 // refinement steps solve the correction in FP64
+    ms::DBuf Y64own;                      // FP64 element buffer of the mixed modes
+    void* Y64 = nullptr;                  // FP64 element products (Y64own, or Y in FP64 mode)
     ms::DBuf Y;                           // element-by-element products [block][ldY]
     ms::DBuf part;                        // 3 * n_vwork partial sums
     ms::DBuf flag;                        // device ints: [0] any active, [1] CTA ticket, [2] error,
@@ -98,6 +103,23 @@ struct mstress_sol_s {
 };
 
 namespace ms {
+
+struct LayoutIn {
+    const mstress_layout* L;
+    double dT;
+    const mstress_bc* bc;
+};
+
+// solve stages (online.cu): build the packed batch of arrays and its work
+// lists; right-hand side, diagonal and lifting; the refinement loop pieces;
+// final residuals and results
+void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in);
+void solve_prepare(mstress_sol_s* s);
+void refine_start(mstress_sol_s* s);
+bool refine_check(mstress_sol_s* s);
+void refine_inner(mstress_sol_s* s);
+void solve_finish(mstress_sol_s* s, bool refined);
+void check_device_error(mstress_sol_s* s);
 
 // global-stage launches (online.cu)
 ApplyArgs apply_args(mstress_sol_s* s, const void* x, const void* z, const PcgState* st, void* Y, bool tc);
@@ -121,6 +143,9 @@ void recover_vm_tc(mstress_sol_s* s, float* out);
 
 // recovery (recover.cu)
 void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev);
+// recovery of the listed arrays only, into a device buffer laid out like the
+// whole batch's output (other arrays' parts are left untouched)
+void recover_arrays(mstress_sol_s* s, int what, void* dst_dev, const std::vector<int>& arrays);
 size_t recover_bytes(const mstress_sol_s* s, int what);
 
 }  // namespace ms
