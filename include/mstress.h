@@ -288,10 +288,14 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
    all iterations and refinement steps), ms4[3] = number of iterations. */
 int mstress_sol_phase_ms(mstress_sol sol, double* ms4);
 
-/* Apply the assembled reduced operator of a layout in FP64 (one matrix-free
-   K_r apply plus interface sum, the kernel pair of every PCG iteration):
+/* Apply the assembled reduced operator of a layout (one matrix-free K_r apply
+   plus interface sum, the kernel pair of every PCG iteration):
    y = A_global x on the lattice vector (X*Y*Z*3 doubles, device pointers).
-   Constrained DOFs are not masked. For testing the operator in isolation. */
+   precision MSTRESS_FP64: FP64 throughout. A reduced mode: x is rounded to
+   FP32 and goes through the inner solver's operator (element products in the
+   mode's operand format with FP32 accumulation, FP32 interface sum); y is the
+   FP32 result widened. Constrained DOFs are not masked. For testing the
+   operator in isolation. */
 int mstress_apply(mstress_ctx ctx, const mstress_layout* layout, const double* x_dev,
                   double* y_dev, int precision);
 

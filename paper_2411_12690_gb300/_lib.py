@@ -36,6 +36,11 @@ MSTRESS_SIGMA_GP = 2
 MSTRESS_U_NODE = 3
 MSTRESS_LATTICE = 4
 
+MSTRESS_RQ_QUEUED = 0
+MSTRESS_RQ_RUNNING = 1
+MSTRESS_RQ_DONE = 2
+MSTRESS_RQ_FAILED = 3
+
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ENOT_CONVERGED", -4: "EDEVICE_TIMEOUT",
                 -5: "ENUMERIC", -6: "ECUDA"}
 

@@ -5,7 +5,11 @@
 //                   for 32 blocks (blockDim.x == 256)
 //   apply32_item    reduced precision on CUDA cores (fallback when the tensor
 //                   core tile does not fit), 32 blocks (blockDim.x == 256)
-//   apply_tc_item   tcgen05 tensor cores, up to 128 blocks (any multiple of 128 threads)
+//   apply_tc_item   tcgen05 tensor cores, up to 128 blocks (any multiple of 128 threads),
+//                   operator resident in shared memory (small bases)
+//   apply_tcs_item  tcgen05 tensor cores for large bases: the operator and the
+//                   gathered coefficients are streamed through a ring of
+//                   shared-memory stages along K
 // Every item gathers its blocks' element DOFs straight from the lattice
 // vector, optionally forming the search direction z + beta p on the fly.
 #pragma once
@@ -256,6 +260,167 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     __syncthreads();
     tc::fence_after();
     return true;
+}
+
+// ------------------------------------------- tensor cores, streamed along K
+// Large bases (m > 80): K_r does not fit in shared memory next to the
+// coefficient tile, so both operands move through `stages` ring slots of ck
+// K-elements each (two MMA K steps). Slot c of the operator image is one
+// contiguous block in global memory, fetched with a single bulk copy that runs
+// while the CTA gathers the matching coefficient columns. An mbarrier per slot
+// counts the copy's bytes (full); a tcgen05.commit per slot frees it once
+// its MMAs are done (empty). N (= m padded to 16) is split into MMAs of at
+// most 256 columns; the accumulator takes npad TMEM columns.
+struct TcsShape {
+    int m, esz, ns, ck, nck, kpad, npad, n0, n1, tmem_cols, stages;
+    uint32_t a_plane, b_plane;   // bytes of one plane of a slot: A 128 x ck, B npad x ck
+    uint32_t a_stage, b_stage;   // bytes of all planes of a slot
+    size_t smem;
+};
+
+struct TcsState {
+    uint8_t* slots;        // stages x (A slot | B slot)
+    uint64_t* full;        // [stages] operator copy landed
+    uint64_t* empty;       // [stages] MMAs reading the slot are done
+    uint32_t tmem;
+    uint32_t chunk;        // slots used so far by this CTA (sets slot and parity)
+};
+
+}  // namespace ai
+
+ai::TcsShape tcs_shape(int m, int prec);   // streamed tensor-core apply geometry (tc.cu)
+
+namespace ai {
+
+// D (128 x npad) = C (tile blocks x K) * K_r^T for one tile, K streamed.
+// Returns false if a wait timed out (the caller stops and reports it).
+template <int MODE>
+__device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShape& sh, const ApplyWork& it,
+                                               TcsState& ts, long long* base, int* offs) {
+    constexpr bool TF32 = MODE == MSTRESS_TF32;
+    constexpr int GU = 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x, nw = nt >> 5;
+    const int m = a.m;
+    const ArrayDev A = a.arrays[it.array];
+    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    const float* __restrict__ z = static_cast<const float*>(a.z);
+    float* __restrict__ Y = static_cast<float*>(a.Y);
+    const uint8_t* img = static_cast<const uint8_t*>(a.tt.Klp[it.type]);
+    tile_setup(a, it, A, base, offs, kTileTC);
+    __syncthreads();
+    const uint32_t sbo = tc::sbo_bytes(sh.ck, sh.esz);
+    const uint32_t slot_bytes = sh.a_stage + sh.b_stage;
+    const int ck_shift = __ffs(sh.ck) - 1;   // ck is a power of two
+    bool ok = true;
+    uint32_t last = 0;
+    for (int c = 0; c < sh.nck; ++c) {
+        const uint32_t g = ts.chunk++, slot = g % (uint32_t)sh.stages, use = g / (uint32_t)sh.stages;
+        uint8_t* sA = ts.slots + slot * slot_bytes;
+        uint8_t* sB = sA + sh.a_stage;
+        last = g;
+        if (use > 0 && ok) ok = tc::mbar_wait(&ts.empty[slot], (use - 1) & 1u, 1 << 24);
+        if (__syncthreads_or(!ok)) return false;
+        if (tid == 0) {
+            tc::mbar_expect_tx(&ts.full[slot], sh.b_stage);
+            tc::bulk_g2s(sB, img + (size_t)c * sh.b_stage, sh.b_stage, &ts.full[slot]);
+        }
+        // gather columns [c ck, (c+1) ck) of the tile; consecutive threads take
+        // consecutive DOFs of one block (contiguous runs in the lattice)
+        const int k0 = c * sh.ck, total = kTileTC * sh.ck;
+        for (int idx0 = tid; idx0 < total; idx0 += nt * GU) {
+            float v[GU];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int idx = idx0 + u * nt, b = idx >> ck_shift, k = k0 + (idx & (sh.ck - 1));
+                v[u] = 0.f;
+                if (idx < total && b < it.count && k < m) v[u] = gather(x, z, base[b] + offs[k], beta);
+            }
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int idx = idx0 + u * nt;
+                if (idx < total)
+                    put_operand(sA, sh.a_plane, tc::operand_offset(idx >> ck_shift, idx & (sh.ck - 1), sh.ck, sh.esz),
+                                v[u], MODE);
+            }
+        }
+        tc::fence_smem_async();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            ok = tc::mbar_wait(&ts.full[slot], use & 1u, 1 << 24);
+            if (ok) {
+                const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+                const uint32_t id0 = tc::instr_desc(TF32, kTileTC, sh.n0);
+                const uint32_t id1 = tc::instr_desc(TF32, kTileTC, sh.n1 > 0 ? sh.n1 : 16);
+                const uint32_t b1 = (uint32_t)(sh.n0 >> 3) * sbo;   // row n0 of the operator slot
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t ko = (uint32_t)j * 2 * tc::kLBO;
+                    // products (A plane, B plane): (hi, hi) [, (lo, hi), (hi, lo)]
+#pragma unroll
+                    for (int pr = 0; pr < (MODE == MSTRESS_BF16X3 ? 3 : 1); ++pr) {
+                        const uint32_t pa = pr == 1 ? sh.a_plane : 0u, pb = pr == 2 ? sh.b_plane : 0u;
+                        const uint32_t acc = (c > 0 || j > 0 || pr > 0) ? 1u : 0u;
+                        const uint64_t da = tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo);
+                        tc::mma<TF32>(ts.tmem, da, tc::smem_desc(b0 + pb + ko, tc::kLBO, sbo), id0, acc);
+                        if (sh.n1 > 0)
+                            tc::mma<TF32>(ts.tmem + (uint32_t)sh.n0, da,
+                                          tc::smem_desc(b0 + pb + b1 + ko, tc::kLBO, sbo), id1, acc);
+                    }
+                }
+                tc::commit(&ts.empty[slot]);
+            }
+        }
+    }
+    if (__syncthreads_or(!ok)) return false;
+    // all MMAs of the tile are done once the last slot's commit has arrived
+    ok = tc::mbar_wait(&ts.empty[last % (uint32_t)sh.stages], (last / (uint32_t)sh.stages) & 1u, 1 << 24);
+    tc::fence_after();
+    if (__syncthreads_or(!ok)) return false;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one block each) and
+    // column chunks 16 (w / 4), 16 (w / 4 + nw / 4), ...
+    const int b = (warp & 3) * 32 + lane;
+    const long long e = b < it.count ? a.blist[it.start + b] : 0;
+    for (int c0 = 16 * (warp >> 2); c0 < sh.npad; c0 += 16 * (nw >> 2)) {
+        float v[16];
+        tc::tmem_ld16(ts.tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
+        if (b < it.count) {
+            float4* dst = reinterpret_cast<float4*>(Y + e * a.ldY + c0);
+            dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+            dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+            dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+            dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return true;
+}
+
+// Set up the slot barriers of a streamed tensor-core CTA (all threads call).
+__device__ __forceinline__ void tcs_init(TcsState& ts, const TcsShape& sh, uint8_t* smem, uint64_t* bars) {
+    ts.slots = smem;
+    ts.full = bars;
+    ts.empty = bars + sh.stages;
+    ts.chunk = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 2 * sh.stages; ++i) tc::mbar_init(&bars[i], 1);
+}
+
+// Bounded drain before a streamed tensor-core CTA exits after a failed wait:
+// let outstanding operator copies and MMAs finish so that neither writes
+// shared or tensor memory after the CTA is gone.
+__device__ __forceinline__ void tcs_drain(const TcsState& ts, const TcsShape& sh) {
+    if (threadIdx.x != 0 || ts.chunk == 0) return;
+    const uint32_t n = ts.chunk < (uint32_t)sh.stages ? ts.chunk : (uint32_t)sh.stages;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t g = ts.chunk - 1 - i, slot = g % (uint32_t)sh.stages, use = g / (uint32_t)sh.stages;
+        tc::mbar_wait(&ts.full[slot], use & 1u, 1 << 20);
+        tc::mbar_wait(&ts.empty[slot], use & 1u, 1 << 20);
+    }
 }
 
 }  // namespace ai

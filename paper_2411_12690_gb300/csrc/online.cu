@@ -302,6 +302,16 @@ __global__ void k_add_bc(long long n, double* x, const double* xbc) {
     if (i < n) x[i] += xbc[i];
 }
 
+__global__ void k_narrow(long long n, const double* x, float* y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+
+__global__ void k_widen(long long n, const float* x, double* y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (double)x[i];
+}
+
 __global__ void k_lift_rhs(long long n, double* b, const double* Axbc, const double* dinv) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n && dinv[i] != 0.0) b[i] -= Axbc[i];
@@ -825,6 +835,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     alloc_into(ctx, s->flag, 64);
     alloc_into(ctx, s->tickets, 2 * (size_t)s->n_arrays * sizeof(int));
     alloc_into(ctx, s->timers, 4 * sizeof(unsigned long long));
+    alloc_into(ctx, s->barrier, 10 * 32 * sizeof(unsigned));
     const bool mixed = s->precision != MSTRESS_FP64;
     alloc_into(ctx, s->Y, (size_t)s->n_blocks * s->ldY * (mixed ? sizeof(float) : sizeof(double)), false);
     if (mixed) {
@@ -1074,17 +1085,28 @@ int mstress_apply(mstress_ctx ctx, const mstress_layout* layout, const double* x
     if (!ctx) return MSTRESS_EINVAL;
     MS_API_BEGIN
     MS_REQUIRE(x_dev && y_dev, MSTRESS_EINVAL, "x and y are required");
-    MS_REQUIRE(precision == MSTRESS_FP64, MSTRESS_EINVAL, "mstress_apply supports MSTRESS_FP64");
+    MS_REQUIRE(precision >= MSTRESS_FP64 && precision <= MSTRESS_BF16X3, MSTRESS_EINVAL, "unknown precision");
     std::unique_ptr<mstress_sol_s> s(new mstress_sol_s());
     s->ctx = ctx;
-    s->precision = MSTRESS_FP64;
+    s->precision = precision;
     mstress_bc bc{1, 0, nullptr, nullptr, 0};
     std::vector<LayoutIn> in{LayoutIn{layout, 0.0, &bc}};
     validate_and_build(s.get(), in);
-    launch_apply(s.get(), MSTRESS_FP64, x_dev, nullptr, false, nullptr, s->Y.ptr);
-    launch_isum(s.get(), s->Y.ptr, false, const_cast<double*>(x_dev), nullptr, y_dev, false, nullptr, nullptr,
-                nullptr);
-    MS_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaStream_t st = ctx->stream;
+    if (precision == MSTRESS_FP64) {
+        launch_apply(s.get(), MSTRESS_FP64, x_dev, nullptr, false, nullptr, s->Y.ptr);
+        launch_isum(s.get(), s->Y.ptr, false, const_cast<double*>(x_dev), nullptr, y_dev, false, nullptr, nullptr,
+                    nullptr);
+    } else {   // x rounded to FP32, the inner solver's operator, y widened
+        const unsigned g = (unsigned)((s->n_vec + 255) / 256);
+        k_narrow<<<g, 256, 0, st>>>(s->n_vec, x_dev, s->v32.x.as<float>());
+        MS_LAUNCH_CHECK();
+        launch_apply(s.get(), precision, s->v32.x.ptr, nullptr, true, nullptr, s->Y.ptr);
+        launch_isum(s.get(), s->Y.ptr, true, s->v32.x.ptr, nullptr, s->v32.q.ptr, true, nullptr, nullptr, nullptr);
+        k_widen<<<g, 256, 0, st>>>(s->n_vec, s->v32.q.as<float>(), y_dev);
+        MS_LAUNCH_CHECK();
+    }
+    MS_CUDA(cudaStreamSynchronize(st));
     MS_API_END(ctx)
 }
 

@@ -10,9 +10,12 @@
 //   C  x += alpha p, r -= alpha q, z = D^-1 r and the <r,z>, <r,r> partials,
 //      folded the same way into beta, the stopping test and the iteration count.
 // The folds are ordered by work-item index only, so an array's arithmetic is
-// the same alone and inside any batch. The grid barrier and the tensor-core
-// completion wait both spin with an iteration limit; on expiry the kernel
-// records an error, releases its tensor memory and returns.
+// the same alone and inside any batch. A CTA reports its finished work items
+// of an array with one atomic per array per phase (not one per item), and
+// reads an array's scalars once per phase. The grid barrier is two-level (8
+// arrival counters on separate cache lines, then a root) and, like the
+// tensor-core completion wait, spins with an iteration limit; on expiry the
+// kernel records an error, releases its tensor memory and returns.
 #include <algorithm>
 
 #include "apply_items.cuh"
@@ -21,13 +24,16 @@
 namespace ms {
 namespace {
 
-enum { AM_FP64 = 0, AM_TC = 1, AM_SIMT32 = 2 };
-constexpr int kPT = 256;   // threads per CTA
+enum { AM_FP64 = 0, AM_TC = 1, AM_SIMT32 = 2, AM_TCS = 3 };
+constexpr int kBarLine = 32;   // unsigned words per barrier cache line
+// barrier words: sub-counters at kBarLine * g (g < 8), root at 8 kBarLine, generation at 9 kBarLine
+constexpr int kBarRoot = 8 * kBarLine, kBarGen = 9 * kBarLine;
 
 struct PcgArgs {
     ApplyArgs ap;              // x = p, z = z, st, Y
     int apply_items, panels;   // work items of phase A; row panels per 32-block tile (CUDA-core apply)
     ai::TcShape sh;
+    ai::TcsShape shs;          // streamed tensor-core apply (large bases)
     const VecWork* vwork;
     int n_vwork;
     const ArrayDev* arrays;
@@ -38,7 +44,7 @@ struct PcgArgs {
     PcgState* st;
     double *part_pq, *part_rz, *part_rr;
     int* tickets;              // 2 per array: phase B, phase C
-    unsigned* bar;             // [0] arrivals, [1] generation
+    unsigned* bar;             // barrier words (see kBarRoot, kBarGen)
     int* n_active;             // arrays still iterating
     int* err;                  // 1: tensor-core wait expired, 2: grid barrier expired
     int* abort;
@@ -62,20 +68,33 @@ __device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned
     }
 }
 
-// Grid-wide barrier with a bounded wait. Returns false (in every thread of the
-// CTA) when the grid is aborting or the wait expired.
+// Two-level grid barrier with a bounded wait. CTA b arrives on sub-counter
+// b % 8; the last arrival of each group arrives on the root; the last root
+// arrival resets the counters and advances the generation that everyone
+// waits on. Returns false (in every thread of the CTA) when the grid is
+// aborting or the wait expired.
 __device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* gen = a.bar + 1;
+        volatile unsigned* gen = a.bar + kBarGen;
         const unsigned g = *gen;            // read before arriving: cannot advance without us
+        const unsigned G = gridDim.x, grp = blockIdx.x & 7u;
+        const unsigned groups = G < 8u ? G : 8u;
+        const unsigned gsize = (G - grp + 7u) / 8u;   // CTAs b < G with b % 8 == grp
         __threadfence();
-        const unsigned arrived = atomicAdd(a.bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(a.bar, 0u);
+        bool last = false;
+        if (atomicAdd(a.bar + kBarLine * grp, 1u) == gsize - 1u) {
+            atomicExch(a.bar + kBarLine * grp, 0u);
             __threadfence();
-            atomicAdd(a.bar + 1, 1u);
+            if (atomicAdd(a.bar + kBarRoot, 1u) == groups - 1u) {
+                atomicExch(a.bar + kBarRoot, 0u);
+                last = true;
+            }
+        }
+        if (last) {
+            __threadfence();
+            atomicAdd(a.bar + kBarGen, 1u);
         } else {
             long long spins = 0;
             while (*gen == g) {
@@ -86,7 +105,7 @@ __device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -97,23 +116,40 @@ __device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok) {
     return *s_ok != 0;
 }
 
-template <class V, int AM, int MODE, int RPT>
-__global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) {
+// Per-CTA bookkeeping of the work items of the array being processed.
+struct ArrayCursor {
+    int k, count;   // array, items done by this CTA in this phase run
+};
+
+template <class V, int AM, int MODE, int RPT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArgs a) {
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ long long base[kTileTC];
     __shared__ int offs[3 * kMaxSurf];
-    __shared__ double shr[kPT / 32], sh8[8];
-    __shared__ int s_flag, s_ok;
+    __shared__ double shr[NT / 32], sh8[8];
+    __shared__ int s_flag, s_ok, s_active;
+    __shared__ double s_scalar;
+    __shared__ ArrayDev s_A;
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t bars[8];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x;
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
     ai::TcState ts;
-    if (AM == AM_TC) {
+    ai::TcsState tss;
+    if constexpr (AM == AM_TCS) {
+        ai::tcs_init(tss, a.shs, smem, bars);
+        if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.shs.tmem_cols);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        tss.tmem = tmem_base;
+    }
+    if constexpr (AM == AM_TC) {
         ts.sB = smem;
         ts.sA = smem + NS * a.sh.b_plane;
-        for (uint32_t i = tid; i < NS * a.sh.a_plane / 16; i += kPT)
+        for (uint32_t i = tid; i < NS * a.sh.a_plane / 16; i += NT)
             reinterpret_cast<uint4*>(ts.sA)[i] = make_uint4(0, 0, 0, 0);
         if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.sh.tmem_cols);
         if (tid == 0) tc::mbar_init(&mbar, 1);
@@ -130,6 +166,79 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
     V* z = static_cast<V*>(a.z);
     V* p = static_cast<V*>(a.p);
     V* q = static_cast<V*>(a.q);
+
+    // Switch the cursor to array k: report the items finished for the previous
+    // array (one atomic; the last reporter folds), then read k's scalars.
+    // phase 1: fold <p,q> into alpha; phase 2: fold <r,z>, <r,r> into beta.
+    auto switch_array = [&](ArrayCursor& cur, int k, int phase) {
+        if (cur.k >= 0 && cur.count > 0) {
+            const int kk = cur.k;
+            if (tid == 0) {
+                __threadfence();
+                const int old = atomicAdd(&a.tickets[2 * kk + phase - 1], cur.count);
+                s_flag = old + cur.count == s_A.n_vwork;
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                if (phase == 1) {
+                    const double pq = pi::cta_fold8(a.part_pq + s_A.vwork_off, s_A.n_vwork, sh8);
+                    if (tid == 0) {
+                        a.tickets[2 * kk] = 0;
+                        const double al = __ldcg(&a.st[kk].rz) / pq;
+                        if (!(pq > 0) || !isfinite(al)) {
+                            a.st[kk].alpha = 0.0;
+                            a.st[kk].active = 0;
+                            a.st[kk].status = MSTRESS_ENUMERIC;
+                            atomicSub(a.n_active, 1);
+                        } else {
+                            a.st[kk].alpha = al;
+                        }
+                    }
+                } else {
+                    const double rz = pi::cta_fold8(a.part_rz + s_A.vwork_off, s_A.n_vwork, sh8);
+                    const double rr = pi::cta_fold8(a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8);
+                    if (tid == 0) {
+                        a.tickets[2 * kk + 1] = 0;
+                        PcgState s;
+                        s.rz = __ldcg(&a.st[kk].rz);
+                        s.tol2 = __ldcg(&a.st[kk].tol2);
+                        s.iters = __ldcg(&a.st[kk].iters) + 1;
+                        s.max_iter = __ldcg(&a.st[kk].max_iter);
+                        int active = 1, status = MSTRESS_OK;
+                        double beta = 0;
+                        if (!isfinite(rz) || !isfinite(rr)) {
+                            active = 0;
+                            status = MSTRESS_ENUMERIC;
+                        } else {
+                            beta = rz / s.rz;
+                            if (rr <= s.tol2) active = 0;
+                            else if (s.iters >= s.max_iter) { active = 0; status = MSTRESS_ENOT_CONVERGED; }
+                        }
+                        a.st[kk].beta = beta;
+                        a.st[kk].rz = rz;
+                        a.st[kk].rr = rr;
+                        a.st[kk].iters = s.iters;
+                        a.st[kk].status = status;
+                        a.st[kk].active = active;
+                        if (!active) atomicSub(a.n_active, 1);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        cur.k = k;
+        cur.count = 0;
+        if (k >= 0) {
+            if (tid == 0) {
+                s_A = a.arrays[k];
+                s_active = __ldcg(&a.st[k].active);
+                s_scalar = phase == 1 ? __ldcg(&a.st[k].beta) : __ldcg(&a.st[k].alpha);
+            }
+            __syncthreads();
+        }
+    };
+
     unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
@@ -137,14 +246,21 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
         for (int w = blockIdx.x; w < a.apply_items; w += gridDim.x) {
             if constexpr (AM == AM_TC) {
                 const ApplyWork it = a.ap.work[w];
-                if (!a.st[it.array].active) continue;
+                if (!__ldcg(&a.st[it.array].active)) continue;
                 if (!ai::apply_tc_item<MODE>(a.ap, a.sh, it, ts, base, offs)) {
+                    failed = true;
+                    break;
+                }
+            } else if constexpr (AM == AM_TCS) {
+                const ApplyWork it = a.ap.work[w];
+                if (!__ldcg(&a.st[it.array].active)) continue;
+                if (!ai::apply_tcs_item<MODE>(a.ap, a.shs, it, tss, base, offs)) {
                     failed = true;
                     break;
                 }
             } else {
                 const ApplyWork it = a.ap.work[w / a.panels];
-                if (!a.st[it.array].active) continue;
+                if (!__ldcg(&a.st[it.array].active)) continue;
                 __syncthreads();
                 if constexpr (AM == AM_FP64)
                     ai::apply64_item<RPT>(a.ap, it, w % a.panels, reinterpret_cast<double*>(smem),
@@ -162,105 +278,73 @@ __global__ void __launch_bounds__(kPT) k_pcg(const __grid_constant__ PcgArgs a) 
         if (!grid_sync(a, &s_ok)) break;
         phase_mark(a, 0, t_prev);
         // ---- phase B: interface sum, <p, q>, alpha
-        for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
-            const VecWork it = a.vwork[w];
-            const int k = it.array;
-            if (!a.st[k].active) continue;
-            const ArrayDev A = a.arrays[k];
-            const double acc = pi::isum_item<V, V>(it, A, a.lm, a.dinv, a.ap.ldY, static_cast<const V*>(a.ap.Y), p, z,
-                                                   q, a.st[k].beta);
-            const double t = pi::block_sum(acc, shr);
-            if (tid == 0) {
-                a.part_pq[w] = t;
-                __threadfence();
-                s_flag = atomicAdd(&a.tickets[2 * k], 1) == A.n_vwork - 1;
+        {
+            ArrayCursor cur{-1, 0};
+            for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+                const VecWork it = a.vwork[w];
+                if (it.array != cur.k) switch_array(cur, it.array, 1);
+                if (!s_active) continue;
+                const double acc = pi::isum_item<V, V>(it, s_A, a.lm, a.dinv, a.ap.ldY, static_cast<const V*>(a.ap.Y),
+                                                       p, z, q, s_scalar);
+                const double t = pi::block_sum(acc, shr);
+                if (tid == 0) a.part_pq[w] = t;
+                cur.count += 1;
             }
-            __syncthreads();
-            if (s_flag) {
-                __threadfence();
-                const double pq = pi::cta_fold8(a.part_pq + A.vwork_off, A.n_vwork, sh8);
-                if (tid == 0) {
-                    a.tickets[2 * k] = 0;
-                    const double al = a.st[k].rz / pq;
-                    if (!(pq > 0) || !isfinite(al)) {
-                        a.st[k].alpha = 0.0;
-                        a.st[k].active = 0;
-                        a.st[k].status = MSTRESS_ENUMERIC;
-                        atomicSub(a.n_active, 1);
-                    } else {
-                        a.st[k].alpha = al;
-                    }
-                }
-            }
-            __syncthreads();
+            switch_array(cur, -1, 1);
         }
         if (!grid_sync(a, &s_ok)) break;
         phase_mark(a, 1, t_prev);
         // ---- phase C: vector update, <r,z>, <r,r>, beta, stopping test
-        for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
-            const VecWork it = a.vwork[w];
-            const int k = it.array;
-            if (!a.st[k].active) continue;
-            const ArrayDev A = a.arrays[k];
-            double srz, srr;
-            pi::vec1_item<V>(it, a.dinv, a.st[k].alpha, x, r, z, p, q, srz, srr);
-            srz = pi::block_sum(srz, shr);
-            srr = pi::block_sum(srr, shr);
-            if (tid == 0) {
-                a.part_rz[w] = srz;
-                a.part_rr[w] = srr;
-                __threadfence();
-                s_flag = atomicAdd(&a.tickets[2 * k + 1], 1) == A.n_vwork - 1;
-            }
-            __syncthreads();
-            if (s_flag) {
-                __threadfence();
-                const double rz = pi::cta_fold8(a.part_rz + A.vwork_off, A.n_vwork, sh8);
-                const double rr = pi::cta_fold8(a.part_rr + A.vwork_off, A.n_vwork, sh8);
+        {
+            ArrayCursor cur{-1, 0};
+            for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+                const VecWork it = a.vwork[w];
+                if (it.array != cur.k) switch_array(cur, it.array, 2);
+                if (!s_active) continue;
+                double srz, srr;
+                pi::vec1_item<V>(it, a.dinv, s_scalar, x, r, z, p, q, srz, srr);
+                srz = pi::block_sum(srz, shr);
+                srr = pi::block_sum(srr, shr);
                 if (tid == 0) {
-                    a.tickets[2 * k + 1] = 0;
-                    PcgState s = a.st[k];
-                    s.iters += 1;
-                    if (!isfinite(rz) || !isfinite(rr)) {
-                        s.active = 0;
-                        s.status = MSTRESS_ENUMERIC;
-                    } else {
-                        s.beta = rz / s.rz;
-                        s.rz = rz;
-                        s.rr = rr;
-                        if (rr <= s.tol2) { s.active = 0; s.status = MSTRESS_OK; }
-                        else if (s.iters >= s.max_iter) { s.active = 0; s.status = MSTRESS_ENOT_CONVERGED; }
-                    }
-                    a.st[k] = s;
-                    if (!s.active) atomicSub(a.n_active, 1);
+                    a.part_rz[w] = srz;
+                    a.part_rr[w] = srr;
                 }
+                cur.count += 1;
             }
-            __syncthreads();
+            switch_array(cur, -1, 2);
         }
         if (!grid_sync(a, &s_ok)) break;
         phase_mark(a, 2, t_prev);
         if (a.timers && blockIdx.x == 0 && tid == 0) a.timers[3] += 1;
         if (*(volatile int*)a.n_active <= 0) break;
     }
-    if (AM == AM_TC) {
+    if constexpr (AM == AM_TC) {
         if (*(volatile int*)a.abort) tc::mbar_wait(&mbar, ts.phase ^ 1u, 1 << 20);   // bounded drain
         tc::fence_before();
         __syncthreads();
         if ((tid >> 5) == 0) tc::tmem_free(ts.tmem, (uint32_t)a.sh.tmem_cols);
     }
+    if constexpr (AM == AM_TCS) {
+        if (*(volatile int*)a.abort) ai::tcs_drain(tss, a.shs);
+        tc::fence_before();
+        __syncthreads();
+        if ((tid >> 5) == 0) tc::tmem_free(tss.tmem, (uint32_t)a.shs.tmem_cols);
+    }
 }
 
-template <class KER>
+template <int NT, class KER>
 bool launch_coop(KER kernel, mstress_sol_s* s, PcgArgs& a, size_t smem, int needed, int tmem_cols) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
     if (e != cudaSuccess || per_sm < 1) { cudaGetLastError(); return false; }
     if (tmem_cols > 0) per_sm = std::min(per_sm, 512 / tmem_cols);
+    per_sm = std::min(per_sm, 4);   // more CTAs only lengthen the barriers
     const int grid = std::max(1, std::min(needed, per_sm * s->ctx->num_sms));
     void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((void*)kernel, grid, kPT, args, smem, s->ctx->stream);
+    e = cudaLaunchCooperativeKernel((void*)kernel, grid, NT, args, smem, s->ctx->stream);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     note_launches(1);
     return true;
@@ -295,11 +379,12 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     int* flag = s->flag.as<int>();
     a.err = flag + 2;
     a.n_active = flag + 4;
-    a.bar = reinterpret_cast<unsigned*>(flag + 5);
     a.abort = flag + 7;
+    a.bar = s->barrier.as<unsigned>();
     a.max_loops = max_iter + 1;
     a.timers = s->timers.as<unsigned long long>();
-    MS_CUDA(cudaMemsetAsync(flag + 5, 0, 3 * sizeof(int), s->ctx->stream));
+    MS_CUDA(cudaMemsetAsync(flag + 7, 0, sizeof(int), s->ctx->stream));
+    MS_CUDA(cudaMemsetAsync(s->barrier.ptr, 0, s->barrier.bytes, s->ctx->stream));
     MS_CUDA(cudaMemsetAsync(s->tickets.ptr, 0, s->tickets.bytes, s->ctx->stream));
     const int m = s->m;
     const int vneed = s->n_vwork;
@@ -308,12 +393,29 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
             a.panels = (m + 15) / 16;
             a.apply_items = s->n_awork * a.panels;
             const size_t smem = (size_t)(m * kTile64 + 16 * m) * sizeof(double) + 1024;
-            return launch_coop(k_pcg<double, AM_FP64, MSTRESS_FP64, 2>, s, a, smem, std::max(a.apply_items, vneed), 0);
+            return launch_coop<256>(k_pcg<double, AM_FP64, MSTRESS_FP64, 2, 256, 2>, s, a, smem,
+                                    std::max(a.apply_items, vneed), 0);
         }
         a.panels = (m + 31) / 32;
         a.apply_items = s->n_awork * a.panels;
         const size_t smem = (size_t)(m * kTile64 + 32 * m) * sizeof(double) + 1024;
-        return launch_coop(k_pcg<double, AM_FP64, MSTRESS_FP64, 4>, s, a, smem, std::max(a.apply_items, vneed), 0);
+        return launch_coop<256>(k_pcg<double, AM_FP64, MSTRESS_FP64, 4, 256, 2>, s, a, smem,
+                                std::max(a.apply_items, vneed), 0);
+    }
+    if (tc && tc_streamed(m)) {
+        a.shs = tcs_shape(m, prec);
+        a.apply_items = s->n_awork_tc;
+        a.panels = 1;
+        const int need = std::max(a.apply_items, vneed);
+        const int tm = a.shs.tmem_cols;
+        switch (prec) {
+            case MSTRESS_TF32:
+                return launch_coop<512>(k_pcg<float, AM_TCS, MSTRESS_TF32, 0, 512, 1>, s, a, a.shs.smem, need, tm);
+            case MSTRESS_BF16:
+                return launch_coop<512>(k_pcg<float, AM_TCS, MSTRESS_BF16, 0, 512, 1>, s, a, a.shs.smem, need, tm);
+            default:
+                return launch_coop<512>(k_pcg<float, AM_TCS, MSTRESS_BF16X3, 0, 512, 1>, s, a, a.shs.smem, need, tm);
+        }
     }
     if (tc) {
         a.sh = tc_shape(m, prec);
@@ -322,11 +424,14 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
         const int need = std::max(a.apply_items, vneed);
         switch (prec) {
             case MSTRESS_TF32:
-                return launch_coop(k_pcg<float, AM_TC, MSTRESS_TF32, 0>, s, a, a.sh.smem, need, a.sh.tmem_cols);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 2>, s, a, a.sh.smem, need,
+                                        a.sh.tmem_cols);
             case MSTRESS_BF16:
-                return launch_coop(k_pcg<float, AM_TC, MSTRESS_BF16, 0>, s, a, a.sh.smem, need, a.sh.tmem_cols);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 2>, s, a, a.sh.smem, need,
+                                        a.sh.tmem_cols);
             default:
-                return launch_coop(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0>, s, a, a.sh.smem, need, a.sh.tmem_cols);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 2>, s, a, a.sh.smem, need,
+                                        a.sh.tmem_cols);
         }
     }
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
@@ -336,13 +441,17 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     const size_t smem = (size_t)ns * (m * kTile64 + 8 * rpt * m) * sizeof(float) + 1024;
     const int need = std::max(a.apply_items, vneed);
     if (rpt == 2) {
-        if (prec == MSTRESS_TF32) return launch_coop(k_pcg<float, AM_SIMT32, MSTRESS_TF32, 2>, s, a, smem, need, 0);
-        if (prec == MSTRESS_BF16) return launch_coop(k_pcg<float, AM_SIMT32, MSTRESS_BF16, 2>, s, a, smem, need, 0);
-        return launch_coop(k_pcg<float, AM_SIMT32, MSTRESS_BF16X3, 2>, s, a, smem, need, 0);
+        if (prec == MSTRESS_TF32)
+            return launch_coop<256>(k_pcg<float, AM_SIMT32, MSTRESS_TF32, 2, 256, 2>, s, a, smem, need, 0);
+        if (prec == MSTRESS_BF16)
+            return launch_coop<256>(k_pcg<float, AM_SIMT32, MSTRESS_BF16, 2, 256, 2>, s, a, smem, need, 0);
+        return launch_coop<256>(k_pcg<float, AM_SIMT32, MSTRESS_BF16X3, 2, 256, 2>, s, a, smem, need, 0);
     }
-    if (prec == MSTRESS_TF32) return launch_coop(k_pcg<float, AM_SIMT32, MSTRESS_TF32, 4>, s, a, smem, need, 0);
-    if (prec == MSTRESS_BF16) return launch_coop(k_pcg<float, AM_SIMT32, MSTRESS_BF16, 4>, s, a, smem, need, 0);
-    return launch_coop(k_pcg<float, AM_SIMT32, MSTRESS_BF16X3, 4>, s, a, smem, need, 0);
+    if (prec == MSTRESS_TF32)
+        return launch_coop<256>(k_pcg<float, AM_SIMT32, MSTRESS_TF32, 4, 256, 2>, s, a, smem, need, 0);
+    if (prec == MSTRESS_BF16)
+        return launch_coop<256>(k_pcg<float, AM_SIMT32, MSTRESS_BF16, 4, 256, 2>, s, a, smem, need, 0);
+    return launch_coop<256>(k_pcg<float, AM_SIMT32, MSTRESS_BF16X3, 4, 256, 2>, s, a, smem, need, 0);
 }
 
 }  // namespace ms

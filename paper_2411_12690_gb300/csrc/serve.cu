@@ -118,6 +118,7 @@ void rebuild_batch(mstress_server_s* S) {
         auto it = std::find(old_ids.begin(), old_ids.end(), r.id);
         if (it == old_ids.end()) continue;
         const int oa = (int)(it - old_ids.begin());
+        s->results[a] = old->results[oa];   // inner iterations of the earlier steps
         const ArrayDev& A = s->arrays[a];
         const ArrayDev& OA = old->arrays[oa];
         MS_CUDA(cudaMemcpyAsync(s->v64.x.as<double>() + A.vec_off, old->v64.x.as<double>() + OA.vec_off,

@@ -6,7 +6,7 @@
 
 namespace ms {
 
-constexpr int kVecChunk = 1024;   // lattice DOFs per vector work item (4 per thread of 256)
+constexpr int kVecChunk = 2048;   // lattice DOFs per vector work item
 constexpr int kTile64 = 32;       // blocks per CUDA-core apply / recovery tile
 constexpr int kTileTC = 128;      // blocks per tensor-core apply tile (the MMA M dimension)
 
@@ -90,9 +90,10 @@ struct mstress_sol_s {
     ms::DBuf Y;                           // element-by-element products [block][ldY]
     ms::DBuf part;                        // 3 * n_vwork partial sums
     ms::DBuf flag;                        // device ints: [0] any active, [1] CTA ticket, [2] error,
-                                          // [3] loop count, [4] arrays active, [5..6] grid barrier, [7] abort
+                                          // [3] loop count, [4] arrays active, [7] abort
     ms::DBuf tickets;                     // 2 ints per array (persistent solver folds)
     ms::DBuf timers;                      // 4 u64: ns in phases A, B, C of the persistent solver, loops
+    ms::DBuf barrier;                     // grid-barrier words of the persistent solver
     ms::TypeTab tt{};
     std::vector<ms::ArrayResult> results;
     // CUDA graphs of the iteration loop (conditional WHILE node), by vector precision
@@ -133,6 +134,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
 
 // tensor-core kernels (tc.cu)
 bool tc_supported(int m);
+bool tc_streamed(int m);   // operator streamed along K (large bases) instead of resident
 void configure_tc_kernels();
 void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a);
 void build_tc_operator(mstress_block blk, int prec);   // K_r image for the tensor-core apply

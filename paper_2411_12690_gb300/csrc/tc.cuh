@@ -97,6 +97,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int m
     return done != 0;
 }
 
+// Arrive on the mbarrier and raise its expected transaction count by bytes.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// One bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16); its bytes complete the transaction count of mbar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
 // Each thread of a warp reads 16 consecutive 32-bit columns of its own TMEM
 // lane (lane = 32 * (warp % 4) + lane id), starting at column taddr & 0xffff.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
