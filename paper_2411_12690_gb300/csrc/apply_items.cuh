@@ -24,7 +24,7 @@ __device__ __forceinline__ float round_tf32(float v) { return tc::to_tf32(v); }
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 template <class V>
-__device__ __forceinline__ V gather(const V* x, const V* z, long long g, double beta) {
+__device__ __forceinline__ V gather(const V* x, const V* z, long long g, V beta) {
     return z ? p_next(z[g], x[g], beta) : x[g];
 }
 
@@ -33,7 +33,7 @@ __device__ __forceinline__ V gather(const V* x, const V* z, long long g, double 
 // a round are independent, so they overlap instead of queueing one L2 round
 // trip behind another). store(idx, k, b, v) writes one value.
 template <class V, class Store>
-__device__ __forceinline__ void gather_tile(const V* __restrict__ x, const V* __restrict__ z, double beta, int m,
+__device__ __forceinline__ void gather_tile(const V* __restrict__ x, const V* __restrict__ z, V beta, int m,
                                             int tile_shift, int count, const long long* base, const int* offs,
                                             Store store) {
     constexpr int GU = 8;
@@ -107,7 +107,7 @@ __device__ __forceinline__ void apply32_item(const ApplyArgs& a, const ApplyWork
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
     const int m = a.m;
     const ArrayDev A = a.arrays[it.array];
-    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const float beta = a.st ? (float)a.st[it.array].beta : 0.f;
     const float* __restrict__ x = static_cast<const float*>(a.x);
     const float* __restrict__ z = static_cast<const float*>(a.z);
     float* __restrict__ Y = static_cast<float*>(a.Y);
@@ -158,6 +158,7 @@ __device__ __forceinline__ void apply32_item(const ApplyArgs& a, const ApplyWork
 // ------------------------------------------------------- tensor cores
 struct TcShape {
     int m, esz, kpad, npad, ksteps, tmem_cols, ns;
+    int lg_tile;                 // log2 of the blocks per tile of the solve (rows gathered per tile)
     uint32_t a_plane, b_plane;   // bytes per operand plane (multiples of 1024)
     size_t smem;                 // dynamic shared memory of a CTA using this shape
 };
@@ -177,6 +178,50 @@ __device__ __forceinline__ void put_operand(uint8_t* plane0, uint32_t plane_byte
         if (mode == MSTRESS_BF16X3)
             *reinterpret_cast<__nv_bfloat16*>(plane0 + plane_bytes + off) =
                 __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+__device__ __forceinline__ void put_operand(uint8_t* plane0, uint32_t plane_bytes, uint32_t off, float v, int mode);
+
+// Gather K groups [kg0, kg0 + nkg) of a tile's coefficients into a K-major
+// no-swizzle operand (K group = 16 bytes of K: 8 bf16 or 4 tf32 values; local
+// group kgl of the destination at kgl * 128 bytes, row groups sbo apart). The
+// thread mapping follows the core matrices: consecutive threads take
+// consecutive K values of one row, then the next rows, so a warp's stores fill
+// contiguous shared memory (no bank conflicts) and its loads run along a
+// block's contiguous lattice DOFs. Rows [count, 1 << lg_tile) and columns
+// >= m are written as zeros. Eight values per thread are in flight at a time.
+template <int MODE>
+__device__ __forceinline__ void gather_operand(const float* __restrict__ x, const float* __restrict__ z, float beta,
+                                               int m, int count, const long long* base, const int* offs, int lg_tile,
+                                               int kg0, int nkg, uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo) {
+    constexpr int ESZ = MODE == MSTRESS_TF32 ? 4 : 2;
+    constexpr int LGKE = MODE == MSTRESS_TF32 ? 2 : 3;   // log2 of values per K group
+    constexpr int KE = 1 << LGKE;
+    constexpr int GU = 8;
+    const int nt = blockDim.x;
+    const int total = nkg << (lg_tile + LGKE);
+    const int rmask = (1 << lg_tile) - 1;
+    for (int idx0 = threadIdx.x; idx0 < total; idx0 += nt * GU) {
+        float v[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = idx0 + u * nt;
+            const int b = (idx >> LGKE) & rmask;
+            const int k = ((kg0 + (idx >> (lg_tile + LGKE))) << LGKE) + (idx & (KE - 1));
+            v[u] = 0.f;
+            if (idx < total && b < count && k < m) v[u] = gather(x, z, base[b] + offs[k], beta);
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = idx0 + u * nt;
+            if (idx < total) {
+                const int b = (idx >> LGKE) & rmask;
+                const uint32_t off = (uint32_t)(b >> 3) * sbo + (uint32_t)(idx >> (lg_tile + LGKE)) * 128u +
+                                     (uint32_t)(b & 7) * 16u + (uint32_t)(idx & (KE - 1)) * ESZ;
+                put_operand(plane0, plane_bytes, off, v[u], MODE);
+            }
+        }
     }
 }
 
@@ -201,7 +246,7 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     const int m = a.m;
     const ArrayDev A = a.arrays[it.array];
-    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const float beta = a.st ? (float)a.st[it.array].beta : 0.f;
     const float* __restrict__ x = static_cast<const float*>(a.x);
     const float* __restrict__ z = static_cast<const float*>(a.z);
     float* __restrict__ Y = static_cast<float*>(a.Y);
@@ -212,9 +257,8 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     }
     tile_setup(a, it, A, base, offs, kTileTC);
     __syncthreads();
-    gather_tile(x, z, beta, m, 7, it.count, base, offs, [&](int, int k, int b, float v) {
-        put_operand(ts.sA, sh.a_plane, tc::operand_offset(b, k, sh.kpad, sh.esz), v, MODE);
-    });
+    gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, 0, sh.kpad * sh.esz / 16, ts.sA,
+                         sh.a_plane, tc::sbo_bytes(sh.kpad, sh.esz));
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();
@@ -273,6 +317,7 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
 // most 256 columns; the accumulator takes npad TMEM columns.
 struct TcsShape {
     int m, esz, ns, ck, nck, kpad, npad, n0, n1, tmem_cols, stages;
+    int lg_tile;                 // log2 of the blocks per tile of the solve (rows gathered per tile)
     uint32_t a_plane, b_plane;   // bytes of one plane of a slot: A 128 x ck, B npad x ck
     uint32_t a_stage, b_stage;   // bytes of all planes of a slot
     size_t smem;
@@ -298,11 +343,10 @@ template <int MODE>
 __device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShape& sh, const ApplyWork& it,
                                                TcsState& ts, long long* base, int* offs) {
     constexpr bool TF32 = MODE == MSTRESS_TF32;
-    constexpr int GU = 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x, nw = nt >> 5;
     const int m = a.m;
     const ArrayDev A = a.arrays[it.array];
-    const double beta = a.st ? a.st[it.array].beta : 0.0;
+    const float beta = a.st ? (float)a.st[it.array].beta : 0.f;
     const float* __restrict__ x = static_cast<const float*>(a.x);
     const float* __restrict__ z = static_cast<const float*>(a.z);
     float* __restrict__ Y = static_cast<float*>(a.Y);
@@ -311,7 +355,6 @@ __device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShap
     __syncthreads();
     const uint32_t sbo = tc::sbo_bytes(sh.ck, sh.esz);
     const uint32_t slot_bytes = sh.a_stage + sh.b_stage;
-    const int ck_shift = __ffs(sh.ck) - 1;   // ck is a power of two
     bool ok = true;
     uint32_t last = 0;
     for (int c = 0; c < sh.nck; ++c) {
@@ -325,25 +368,9 @@ __device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShap
             tc::mbar_expect_tx(&ts.full[slot], sh.b_stage);
             tc::bulk_g2s(sB, img + (size_t)c * sh.b_stage, sh.b_stage, &ts.full[slot]);
         }
-        // gather columns [c ck, (c+1) ck) of the tile; consecutive threads take
-        // consecutive DOFs of one block (contiguous runs in the lattice)
-        const int k0 = c * sh.ck, total = kTileTC * sh.ck;
-        for (int idx0 = tid; idx0 < total; idx0 += nt * GU) {
-            float v[GU];
-#pragma unroll
-            for (int u = 0; u < GU; ++u) {
-                const int idx = idx0 + u * nt, b = idx >> ck_shift, k = k0 + (idx & (sh.ck - 1));
-                v[u] = 0.f;
-                if (idx < total && b < it.count && k < m) v[u] = gather(x, z, base[b] + offs[k], beta);
-            }
-#pragma unroll
-            for (int u = 0; u < GU; ++u) {
-                const int idx = idx0 + u * nt;
-                if (idx < total)
-                    put_operand(sA, sh.a_plane, tc::operand_offset(idx >> ck_shift, idx & (sh.ck - 1), sh.ck, sh.esz),
-                                v[u], MODE);
-            }
-        }
+        // gather columns [c ck, (c+1) ck) of the tile (two 32-byte MMA K steps)
+        gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, c * (sh.ck * sh.esz / 16),
+                             sh.ck * sh.esz / 16, sA, sh.a_plane, sbo);
         tc::fence_smem_async();
         tc::fence_before();
         __syncthreads();
@@ -408,6 +435,11 @@ __device__ __forceinline__ void tcs_init(TcsState& ts, const TcsShape& sh, uint8
     ts.chunk = 0;
     if (threadIdx.x == 0)
         for (int i = 0; i < 2 * sh.stages; ++i) tc::mbar_init(&bars[i], 1);
+    // rows at or beyond the solve's tile size are never gathered: keep them zero
+    for (int st = 0; st < sh.stages; ++st) {
+        uint4* a0 = reinterpret_cast<uint4*>(smem + (size_t)st * (sh.a_stage + sh.b_stage));
+        for (uint32_t i = threadIdx.x; i < sh.a_stage / 16; i += blockDim.x) a0[i] = make_uint4(0, 0, 0, 0);
+    }
 }
 
 // Bounded drain before a streamed tensor-core CTA exits after a failed wait:

@@ -122,7 +122,7 @@ struct IsumArgs {
     const ArrayDev* arrays;
     const LocalMap* lm;
     const PcgState* st;     // optional: skip stopped arrays, beta of the p update
-    const double* dinv;     // optional: zero the constrained rows
+    const void* dinv;       // optional, in the vector precision: zero the constrained rows
     int ldY;
     const void* Y;
     void* p;                // direction (updated in place when z is given)
@@ -139,10 +139,10 @@ __global__ void __launch_bounds__(kThreads) k_isum(const __grid_constant__ IsumA
         const VecWork it = a.vwork[w];
         if (a.st && !a.st[it.array].active) continue;
         const ArrayDev A = a.arrays[it.array];
-        const double beta = a.st ? a.st[it.array].beta : 0.0;
-        const double acc = pi::isum_item<V, YT>(it, A, a.lm, a.dinv, a.ldY, static_cast<const YT*>(a.Y),
-                                                static_cast<V*>(a.p), static_cast<const V*>(a.z),
-                                                static_cast<V*>(a.q), beta);
+        const V beta = a.st ? (V)a.st[it.array].beta : V(0);
+        const V acc = pi::isum_item<4, V, YT>(it, A, a.lm, static_cast<const V*>(a.dinv), a.ldY,
+                                              static_cast<const YT*>(a.Y), static_cast<V*>(a.p),
+                                              static_cast<const V*>(a.z), static_cast<V*>(a.q), beta);
         if (a.part_pq) {
             const double t = block_sum(acc, sh);
             if (threadIdx.x == 0) a.part_pq[w] = t;
@@ -158,6 +158,7 @@ struct VecArgs {
     int n_arrays;
     PcgState* st;
     const double* dinv;
+    const void* dinv_v;     // dinv in the vector precision
     void *x, *r, *z, *p, *q;
     const void* rhs;        // init / residual: right-hand side (FP64)
     double *part_pq, *part_rz, *part_rr;
@@ -216,12 +217,12 @@ __global__ void __launch_bounds__(kThreads) k_vec1(const __grid_constant__ VecAr
             if (threadIdx.x == 0) s_alpha = (pq > 0 && isfinite(al)) ? al : 0.0;
         }
         __syncthreads();
-        const double al = s_alpha;
-        double srz, srr;
-        pi::vec1_item<V>(it, a.dinv, al, x, r, z, p, q, srz, srr);
-        srz = block_sum(srz, sh);
-        srr = block_sum(srr, sh);
-        if (threadIdx.x == 0) { a.part_rz[w] = srz; a.part_rr[w] = srr; }
+        const V al = (V)s_alpha;
+        V srz, srr;
+        pi::vec1_item<4, V>(it, static_cast<const V*>(a.dinv_v), al, x, r, z, p, q, srz, srr);
+        const double rz = block_sum(srz, sh);
+        const double rr = block_sum(srr, sh);
+        if (threadIdx.x == 0) { a.part_rz[w] = rz; a.part_rr[w] = rr; }
     }
     // ---- last CTA: per-array scalar phase
     __threadfence();
@@ -427,6 +428,7 @@ VecArgs vec_args(mstress_sol_s* s, PcgVectors& v) {
     a.n_arrays = s->n_arrays;
     a.st = v.state.as<PcgState>();
     a.dinv = s->dinv.as<double>();
+    a.dinv_v = &v == &s->v32 ? s->dinv32.ptr : s->dinv.ptr;
     a.x = v.x.ptr;
     a.r = v.r.ptr;
     a.z = v.z.ptr;
@@ -512,7 +514,7 @@ void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool
 }
 
 void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, void* p, const void* z, void* q, bool vec_fp32,
-                 const double* dinv, const PcgState* st, double* part_pq) {
+                 const void* dinv, const PcgState* st, double* part_pq) {
     IsumArgs a;
     a.vwork = s->d_vwork.as<VecWork>();
     a.n_vwork = s->n_vwork;
@@ -544,7 +546,8 @@ void pcg_iteration(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond, cuda
     cudaStream_t stream = s->ctx->stream;
     const PcgState* st = v.state.as<PcgState>();
     launch_apply(s, prec, v.p.ptr, v.z.ptr, f32, st, s->Y.ptr);
-    launch_isum(s, s->Y.ptr, f32, v.p.ptr, v.z.ptr, v.q.ptr, f32, s->dinv.as<double>(), st, s->part.as<double>());
+    launch_isum(s, s->Y.ptr, f32, v.p.ptr, v.z.ptr, v.q.ptr, f32, f32 ? s->dinv32.ptr : s->dinv.ptr, st,
+                s->part.as<double>());
     VecArgs va = vec_args(s, v);
     va.use_cond = use_cond;
     va.cond = cond;
@@ -885,6 +888,10 @@ void solve_prepare(mstress_sol_s* s) {
     k_rhs_diag<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(ra);
     MS_LAUNCH_CHECK();
     if (s->precision != MSTRESS_FP64) {
+        alloc_into(ctx, s->dinv32, (size_t)s->n_vec * sizeof(float), false);
+        k_narrow<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->dinv.as<double>(),
+                                                                          s->dinv32.as<float>());
+        MS_LAUNCH_CHECK();
         alloc_into(ctx, s->Y64own, (size_t)s->n_blocks * s->ldY * sizeof(double), false);
         s->Y64 = s->Y64own.ptr;
     } else {
@@ -1127,8 +1134,8 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
                 else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, nullptr, false, nullptr, s->Y.ptr);
                 break;
             case 1:
-                if (mixed) launch_isum(s, s->Y.ptr, true, s->v32.p.ptr, nullptr, s->v32.q.ptr, true,
-                                       s->dinv.as<double>(), nullptr, s->part.as<double>());
+                if (mixed) launch_isum(s, s->Y.ptr, true, s->v32.p.ptr, nullptr, s->v32.q.ptr, true, s->dinv32.ptr,
+                                       nullptr, s->part.as<double>());
                 else launch_isum(s, s->Y.ptr, false, s->v64.p.ptr, nullptr, s->v64.q.ptr, false, s->dinv.as<double>(),
                                  nullptr, s->part.as<double>());
                 break;

@@ -48,6 +48,22 @@ __device__ __forceinline__ double cta_fold8(const double* v, int n, double* sh8)
     return t;
 }
 
+// Block sum of FP32 per-thread values in a fixed order: FP32 butterfly within
+// each warp, the warp sums added in FP64 by thread 0 (the FP64 pipe of the
+// GPU is narrow, so only blockDim.x / 32 FP64 additions). Result valid in
+// thread 0.
+__device__ __forceinline__ double block_sum(float v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = (double)v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nw; ++k) t += sh[k];
+    return t;
+}
+
 // Block sum (blockDim.x threads, multiple of 32) in a fixed order; result valid in all threads.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -94,34 +110,33 @@ __device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __r
 
 // Interface sum of one vector work item: q_g = sum of Y_e over the owning
 // blocks (fixed order), p updated to z + beta p when z is given; returns this
-// thread's share of <p, q>.
-// Each thread handles kIsumU DOFs at once and issues all their loads (mask,
+// thread's share of <p, q>. Arithmetic in the vector precision V (dinv, the
+// constrained-row mask, in V as well).
+// Each thread handles U DOFs at once and issues all their loads (mask,
 // direction, up to four owner contributions) before combining, so a work item
-// costs one round trip to L2 instead of a chain of dependent ones. The owner
-// candidates are visited rows ascending then columns ascending, as in
-// for_owners; constrained rows are zeroed after the sum.
-constexpr int kIsumU = 4;
-
-template <class V, class YT>
-__device__ __forceinline__ double isum_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm, const double* dinv,
-                                            int ldY, const YT* __restrict__ Y, V* __restrict__ p,
-                                            const V* __restrict__ z, V* __restrict__ q, double beta) {
+// of U * blockDim.x DOFs costs one round trip to L2 instead of a chain of
+// dependent ones. The owner candidates are visited rows ascending then columns
+// ascending, as in for_owners; constrained rows are zeroed after the sum.
+template <int U, class V, class YT>
+__device__ __forceinline__ V isum_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm, const V* dinv, int ldY,
+                                       const YT* __restrict__ Y, V* __restrict__ p, const V* __restrict__ z,
+                                       V* __restrict__ q, V beta) {
     const int n = lm->n, n1 = n - 1;
     const int16_t* __restrict__ surf = lm->surf_idx;
     const long long end = it.start + it.count;
-    double acc = 0;
-    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * kIsumU) {
-        double s[kIsumU], dv[kIsumU];
-        V pv[kIsumU], zv[kIsumU];
+    V acc = 0;
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
+        V s[U], dv[U];
+        V pv[U], zv[U];
 #pragma unroll
-        for (int u = 0; u < kIsumU; ++u) {
+        for (int u = 0; u < U; ++u) {
             const long long g = g0 + (long long)u * blockDim.x;
             s[u] = 0;
             dv[u] = 0;
             pv[u] = V(0);
             zv[u] = V(0);
             if (g < end) {
-                dv[u] = dinv ? dinv[g] : 1.0;
+                dv[u] = dinv ? dinv[g] : V(1);
                 pv[u] = p[g];
                 if (z) zv[u] = z[g];
                 int comp, gx, gy, gz;
@@ -136,61 +151,62 @@ __device__ __forceinline__ double isum_item(const VecWork& it, const ArrayDev& A
                     if (use) {
                         const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
                         if (sidx >= 0)
-                            s[u] += (double)Y[(A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp];
+                            s[u] += (V)Y[(A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp];
                     }
                 }
             }
         }
 #pragma unroll
-        for (int u = 0; u < kIsumU; ++u) {
+        for (int u = 0; u < U; ++u) {
             const long long g = g0 + (long long)u * blockDim.x;
             if (g < end) {
-                const double sv = dv[u] != 0.0 ? s[u] : 0.0;
+                const V sv = dv[u] != V(0) ? s[u] : V(0);
                 V pn = pv[u];
                 if (z) {
                     pn = p_next(zv[u], pv[u], beta);
                     p[g] = pn;
                 }
-                q[g] = (V)sv;
-                acc += (double)pn * sv;
+                q[g] = sv;
+                acc = fma(pn, sv, acc);
             }
         }
     }
     return acc;
 }
 
-// Vector update of one work item: x += alpha p, r -= alpha q, z = D^-1 r;
-// returns this thread's shares of <r, z> and <r, r>.
-template <class V>
-__device__ __forceinline__ void vec1_item(const VecWork& it, const double* dinv, double al, V* x, V* r, V* z,
-                                          const V* p, const V* q, double& srz, double& srr) {
+// Vector update of one work item: x += alpha p, r -= alpha q, z = D^-1 r in
+// the vector precision V; returns this thread's shares of <r, z> and <r, r>
+// (U DOFs per thread in flight).
+template <int U, class V>
+__device__ __forceinline__ void vec1_item(const VecWork& it, const V* dinv, V al, V* x, V* r, V* z, const V* p,
+                                          const V* q, V& srz, V& srr) {
     srz = 0;
     srr = 0;
     const long long end = it.start + it.count;
-    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * kIsumU) {
-        double pv[kIsumU], qv[kIsumU], xv[kIsumU], rv0[kIsumU], dv[kIsumU];
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
+        V pv[U], qv[U], xv[U], rv0[U], dv[U];
 #pragma unroll
-        for (int u = 0; u < kIsumU; ++u) {   // all loads first
+        for (int u = 0; u < U; ++u) {   // all loads first
             const long long g = g0 + (long long)u * blockDim.x;
             if (g < end) {
-                pv[u] = (double)p[g];
-                qv[u] = (double)q[g];
-                xv[u] = (double)x[g];
-                rv0[u] = (double)r[g];
+                pv[u] = p[g];
+                qv[u] = q[g];
+                xv[u] = x[g];
+                rv0[u] = r[g];
                 dv[u] = dinv[g];
             }
         }
 #pragma unroll
-        for (int u = 0; u < kIsumU; ++u) {
+        for (int u = 0; u < U; ++u) {
             const long long g = g0 + (long long)u * blockDim.x;
             if (g < end) {
-                x[g] = (V)(xv[u] + al * pv[u]);
-                const V rv = (V)(rv0[u] - al * qv[u]);
-                const V zv = (V)(dv[u] * (double)rv);
+                x[g] = fma(al, pv[u], xv[u]);
+                const V rv = fma(-al, qv[u], rv0[u]);
+                const V zv = dv[u] * rv;
                 r[g] = rv;
                 z[g] = zv;
-                srz += (double)rv * (double)zv;
-                srr += (double)rv * (double)rv;
+                srz = fma(rv, zv, srz);
+                srr = fma(rv, rv, srr);
             }
         }
     }

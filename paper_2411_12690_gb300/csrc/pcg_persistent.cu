@@ -39,7 +39,7 @@ struct PcgArgs {
     const ArrayDev* arrays;
     int n_arrays;
     const LocalMap* lm;
-    const double* dinv;
+    const void* dinv;          // Jacobi inverse in the vector precision
     void *x, *r, *z, *p, *q;
     PcgState* st;
     double *part_pq, *part_rz, *part_rr;
@@ -284,8 +284,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 const VecWork it = a.vwork[w];
                 if (it.array != cur.k) switch_array(cur, it.array, 1);
                 if (!s_active) continue;
-                const double acc = pi::isum_item<V, V>(it, s_A, a.lm, a.dinv, a.ap.ldY, static_cast<const V*>(a.ap.Y),
-                                                       p, z, q, s_scalar);
+                const V acc = pi::isum_item<4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
+                                                     static_cast<const V*>(a.ap.Y), p, z, q, (V)s_scalar);
                 const double t = pi::block_sum(acc, shr);
                 if (tid == 0) a.part_pq[w] = t;
                 cur.count += 1;
@@ -301,13 +301,13 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 const VecWork it = a.vwork[w];
                 if (it.array != cur.k) switch_array(cur, it.array, 2);
                 if (!s_active) continue;
-                double srz, srr;
-                pi::vec1_item<V>(it, a.dinv, s_scalar, x, r, z, p, q, srz, srr);
-                srz = pi::block_sum(srz, shr);
-                srr = pi::block_sum(srr, shr);
+                V srz, srr;
+                pi::vec1_item<4, V>(it, static_cast<const V*>(a.dinv), (V)s_scalar, x, r, z, p, q, srz, srr);
+                const double rz = pi::block_sum(srz, shr);
+                const double rr = pi::block_sum(srr, shr);
                 if (tid == 0) {
-                    a.part_rz[w] = srz;
-                    a.part_rr[w] = srr;
+                    a.part_rz[w] = rz;
+                    a.part_rr[w] = rr;
                 }
                 cur.count += 1;
             }
@@ -365,7 +365,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     a.arrays = s->d_arrays.as<ArrayDev>();
     a.n_arrays = s->n_arrays;
     a.lm = s->d_lm.as<LocalMap>();
-    a.dinv = s->dinv.as<double>();
+    a.dinv = vec_fp32 ? s->dinv32.ptr : s->dinv.ptr;
     a.x = v.x.ptr;
     a.r = v.r.ptr;
     a.z = v.z.ptr;
@@ -404,6 +404,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     }
     if (tc && tc_streamed(m)) {
         a.shs = tcs_shape(m, prec);
+        a.shs.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
         const int need = std::max(a.apply_items, vneed);
@@ -419,18 +420,19 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     }
     if (tc) {
         a.sh = tc_shape(m, prec);
+        a.sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
         const int need = std::max(a.apply_items, vneed);
         switch (prec) {
             case MSTRESS_TF32:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 2>, s, a, a.sh.smem, need,
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1>, s, a, a.sh.smem, need,
                                         a.sh.tmem_cols);
             case MSTRESS_BF16:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 2>, s, a, a.sh.smem, need,
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 1>, s, a, a.sh.smem, need,
                                         a.sh.tmem_cols);
             default:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 2>, s, a, a.sh.smem, need,
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 1>, s, a, a.sh.smem, need,
                                         a.sh.tmem_cols);
         }
     }

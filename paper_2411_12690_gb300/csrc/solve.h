@@ -38,11 +38,12 @@ struct ApplyArgs {
     int* err;              // device error word (bounded waits)
 };
 
-// The search-direction update p = z + beta p, written once so that the
-// gather of the apply and the interface sum compute identical bits.
+// The search-direction update p = z + beta p in the vector precision (one
+// fused multiply-add), written once so that the gather of the apply and the
+// interface sum compute identical bits.
 template <class V>
-__device__ __forceinline__ V p_next(V z, V p, double beta) {
-    return (V)fma(beta, (double)p, (double)z);
+__device__ __forceinline__ V p_next(V z, V p, V beta) {
+    return fma(beta, p, z);
 }
 
 // Per-tile gather set-up: lattice base index of each block of the tile and
@@ -81,6 +82,7 @@ struct mstress_sol_s {
     int tc_tile = 128;                    // blocks per tensor-core apply tile (<= 128; smaller tiles
                                           // spread a small array's gather over more SMs)
     ms::DBuf b, dinv, fixed;              // FP64 right-hand side, Jacobi inverse (0 on constrained DOFs)
+    ms::DBuf dinv32;                      // Jacobi inverse in FP32 (inner PCG of the mixed modes)
     ms::DBuf xbc;                         // prescribed values (lifting), or empty
     ms::PcgVectors v64, v32;              // FP64 outer / plain vectors, FP32 inner vectors
     ms::PcgVectors v64i;                  // FP64 inner vectors (refinement with an FP64 inner solve)
@@ -127,7 +129,7 @@ ApplyArgs apply_args(mstress_sol_s* s, const void* x, const void* z, const PcgSt
 void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool vec_fp32, const PcgState* st,
                   void* Y);
 void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, void* p, const void* z, void* q, bool vec_fp32,
-                 const double* dinv, const PcgState* st, double* part_pq);
+                 const void* dinv, const PcgState* st, double* part_pq);   // dinv in the vector precision
 
 // persistent cooperative PCG (pcg_persistent.cu); false if it cannot be launched
 bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter, bool vec_fp32);

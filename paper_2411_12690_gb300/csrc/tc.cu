@@ -31,6 +31,7 @@ ai::TcShape tc_shape(int m, int prec) {
     s.tmem_cols = 32;
     while (s.tmem_cols < s.npad) s.tmem_cols *= 2;
     s.ns = prec == MSTRESS_BF16X3 ? 2 : 1;
+    s.lg_tile = 7;
     s.a_plane = (uint32_t)round_up((int64_t)kTileTC * s.kpad * s.esz, 1024);
     s.b_plane = (uint32_t)round_up((int64_t)s.npad * s.kpad * s.esz, 1024);
     s.smem = (size_t)s.ns * (s.a_plane + s.b_plane) + 1024;   // + alignment slack
@@ -50,6 +51,7 @@ ai::TcsShape tcs_shape(int m, int prec) {
     s.n1 = s.npad - s.n0;
     s.tmem_cols = 32;
     while (s.tmem_cols < s.npad) s.tmem_cols *= 2;
+    s.lg_tile = 7;
     s.a_plane = (uint32_t)(kTileTC * s.ck * s.esz);
     s.b_plane = (uint32_t)(s.npad * s.ck * s.esz);
     s.a_stage = s.ns * s.a_plane;
@@ -219,6 +221,7 @@ void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a) {
     cudaStream_t st = s->ctx->stream;
     if (tc_streamed(s->m)) {
         ai::TcsShape sh = tcs_shape(s->m, prec);
+        sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
         MS_REQUIRE(sh.npad <= 512 && sh.stages >= 2, MSTRESS_EINVAL, "basis too large for the tensor-core tile");
         const int per_sm = sh.tmem_cols <= 256 ? 2 : 1;
         const int grid = std::max(1, std::min(a.n_work, s->ctx->num_sms * per_sm));
@@ -231,6 +234,7 @@ void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a) {
         return;
     }
     ai::TcShape sh = tc_shape(s->m, prec);
+    sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
     MS_REQUIRE(sh.npad <= 256 && sh.smem <= 200 * 1024, MSTRESS_EINVAL, "basis too large for the tensor-core tile");
     const int per_sm = sh.smem > 100 * 1024 ? 1 : 2;   // TMEM: <= 2 x 256 columns per SM
     const int grid = std::max(1, std::min(a.n_work, s->ctx->num_sms * per_sm));
