@@ -351,16 +351,20 @@ def batch_bench(args):
     n_el = W.BLOCK_P15.ex * W.BLOCK_P15.ey * W.BLOCK_P15.ez
     vm = torch.empty(n_blocks * n_el, dtype=torch.float64 if PREC[args.precision] == 0 else torch.float32,
                      device="cuda")
-    times = []
+    times, split = [], []
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sol = ctx.solve_batch(spec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         sol.recover(L.MSTRESS_VM_ELEM, out=vm)
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
+            split.append((t1 - t0, time.perf_counter() - t1))
         infos = [sol.info(a) for a in range(len(jobs))]
+        phases = sol.phase_ms()
         sol.close()
     total = sum(times)
     print(json.dumps({"metric": "TSV blocks solved+recovered/s (256-array batch)", "value": n_blocks * len(times) / total,
@@ -371,7 +375,10 @@ def batch_bench(args):
                                       f"(24x24x20 mesh, degree-4 basis, m=294), dT U[-300,-150] K, one batched solve",
                           "blocks": n_blocks, "max_pcg_iters": max(i["iters"] for i in infos),
                           "max_refinement_steps": max(i["outer"] for i in infos),
-                          "max_rel_res": max(i["rel_res"] for i in infos)}}), flush=True)
+                          "max_rel_res": max(i["rel_res"] for i in infos),
+                          "solve_ms": 1e3 * sum(a for a, _ in split) / len(split),
+                          "recover_ms": 1e3 * sum(b for _, b in split) / len(split),
+                          "persistent_phase_ms": phases}}), flush=True)
 
 
 def serve_bench(args):

@@ -192,36 +192,65 @@ __device__ __forceinline__ void put_operand(uint8_t* plane0, uint32_t plane_byte
 // block's contiguous lattice DOFs. Rows [count, 1 << lg_tile) and columns
 // >= m are written as zeros. Eight values per thread are in flight at a time.
 template <int MODE>
+struct OperandMap {   // element idx of a gathered K-group range -> (row, column, shared-memory offset)
+    static constexpr int ESZ = MODE == MSTRESS_TF32 ? 4 : 2;
+    static constexpr int LGKE = MODE == MSTRESS_TF32 ? 2 : 3;   // log2 of values per K group
+    static constexpr int KE = 1 << LGKE;
+    __device__ __forceinline__ static int row(int idx, int lg_tile) { return (idx >> LGKE) & ((1 << lg_tile) - 1); }
+    __device__ __forceinline__ static int col(int idx, int lg_tile, int kg0) {
+        return ((kg0 + (idx >> (lg_tile + LGKE))) << LGKE) + (idx & (KE - 1));
+    }
+    __device__ __forceinline__ static uint32_t off(int idx, int lg_tile, uint32_t sbo) {
+        const int b = row(idx, lg_tile);
+        return (uint32_t)(b >> 3) * sbo + (uint32_t)(idx >> (lg_tile + LGKE)) * 128u + (uint32_t)(b & 7) * 16u +
+               (uint32_t)(idx & (KE - 1)) * ESZ;
+    }
+};
+
+// One round of the gather: the GU values idx0 + u * blockDim.x (u < GU) of a
+// K-group range, loaded into registers (zero outside the tile's blocks and m).
+template <int MODE, int GU>
+__device__ __forceinline__ void operand_load(const float* __restrict__ x, const float* __restrict__ z, float beta,
+                                             int m, int count, const long long* base, const int* offs, int lg_tile,
+                                             int kg0, int total, int idx0, float (&v)[GU]) {
+    using OM = OperandMap<MODE>;
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+        const int idx = idx0 + u * (int)blockDim.x;
+        const int b = OM::row(idx, lg_tile), k = OM::col(idx, lg_tile, kg0);
+        v[u] = 0.f;
+        if (idx < total && b < count && k < m) v[u] = gather(x, z, base[b] + offs[k], beta);
+    }
+}
+
+template <int MODE, int GU>
+__device__ __forceinline__ void operand_store(int lg_tile, int total, int idx0, const float (&v)[GU], uint8_t* plane0,
+                                              uint32_t plane_bytes, uint32_t sbo) {
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+        const int idx = idx0 + u * (int)blockDim.x;
+        if (idx < total) put_operand(plane0, plane_bytes, OperandMap<MODE>::off(idx, lg_tile, sbo), v[u], MODE);
+    }
+}
+
+// Gather K groups [kg0, kg0 + nkg) of a tile's coefficients into a K-major
+// no-swizzle operand (K group = 16 bytes of K: 8 bf16 or 4 tf32 values; local
+// group kgl of the destination at kgl * 128 bytes, row groups sbo apart). The
+// thread mapping follows the core matrices: consecutive threads take
+// consecutive K values of one row, then the next rows, so a warp's stores fill
+// contiguous shared memory (no bank conflicts) and its loads run along a
+// block's contiguous lattice DOFs. Rows [count, 1 << lg_tile) and columns
+// >= m are written as zeros. Eight values per thread are in flight at a time.
+template <int MODE>
 __device__ __forceinline__ void gather_operand(const float* __restrict__ x, const float* __restrict__ z, float beta,
                                                int m, int count, const long long* base, const int* offs, int lg_tile,
                                                int kg0, int nkg, uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo) {
-    constexpr int ESZ = MODE == MSTRESS_TF32 ? 4 : 2;
-    constexpr int LGKE = MODE == MSTRESS_TF32 ? 2 : 3;   // log2 of values per K group
-    constexpr int KE = 1 << LGKE;
     constexpr int GU = 8;
-    const int nt = blockDim.x;
-    const int total = nkg << (lg_tile + LGKE);
-    const int rmask = (1 << lg_tile) - 1;
-    for (int idx0 = threadIdx.x; idx0 < total; idx0 += nt * GU) {
+    const int total = nkg << (lg_tile + OperandMap<MODE>::LGKE);
+    for (int idx0 = threadIdx.x; idx0 < total; idx0 += (int)blockDim.x * GU) {
         float v[GU];
-#pragma unroll
-        for (int u = 0; u < GU; ++u) {
-            const int idx = idx0 + u * nt;
-            const int b = (idx >> LGKE) & rmask;
-            const int k = ((kg0 + (idx >> (lg_tile + LGKE))) << LGKE) + (idx & (KE - 1));
-            v[u] = 0.f;
-            if (idx < total && b < count && k < m) v[u] = gather(x, z, base[b] + offs[k], beta);
-        }
-#pragma unroll
-        for (int u = 0; u < GU; ++u) {
-            const int idx = idx0 + u * nt;
-            if (idx < total) {
-                const int b = (idx >> LGKE) & rmask;
-                const uint32_t off = (uint32_t)(b >> 3) * sbo + (uint32_t)(idx >> (lg_tile + LGKE)) * 128u +
-                                     (uint32_t)(b & 7) * 16u + (uint32_t)(idx & (KE - 1)) * ESZ;
-                put_operand(plane0, plane_bytes, off, v[u], MODE);
-            }
-        }
+        operand_load<MODE, GU>(x, z, beta, m, count, base, offs, lg_tile, kg0, total, idx0, v);
+        operand_store<MODE, GU>(lg_tile, total, idx0, v, plane0, plane_bytes, sbo);
     }
 }
 
@@ -357,6 +386,15 @@ __device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShap
     const uint32_t slot_bytes = sh.a_stage + sh.b_stage;
     bool ok = true;
     uint32_t last = 0;
+    // When a chunk is one round of loads (blockDim.x * 8 >= its values), the
+    // values of chunk c + 1 are loaded into registers while chunk c is stored
+    // and its MMAs are issued, so one load latency overlaps the next.
+    constexpr int GU = 8;
+    const int nkg = sh.ck * sh.esz / 16;
+    const int total = nkg << (sh.lg_tile + OperandMap<MODE>::LGKE);
+    const bool one_round = total <= nt * GU;
+    float vcur[GU], vnext[GU];
+    if (one_round) operand_load<MODE, GU>(x, z, beta, m, it.count, base, offs, sh.lg_tile, 0, total, tid, vcur);
     for (int c = 0; c < sh.nck; ++c) {
         const uint32_t g = ts.chunk++, slot = g % (uint32_t)sh.stages, use = g / (uint32_t)sh.stages;
         uint8_t* sA = ts.slots + slot * slot_bytes;
@@ -368,9 +406,16 @@ __device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShap
             tc::mbar_expect_tx(&ts.full[slot], sh.b_stage);
             tc::bulk_g2s(sB, img + (size_t)c * sh.b_stage, sh.b_stage, &ts.full[slot]);
         }
-        // gather columns [c ck, (c+1) ck) of the tile (two 32-byte MMA K steps)
-        gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, c * (sh.ck * sh.esz / 16),
-                             sh.ck * sh.esz / 16, sA, sh.a_plane, sbo);
+        if (one_round) {
+            if (c + 1 < sh.nck)
+                operand_load<MODE, GU>(x, z, beta, m, it.count, base, offs, sh.lg_tile, (c + 1) * nkg, total, tid,
+                                       vnext);
+            operand_store<MODE, GU>(sh.lg_tile, total, tid, vcur, sA, sh.a_plane, sbo);
+#pragma unroll
+            for (int u = 0; u < GU; ++u) vcur[u] = vnext[u];
+        } else {
+            gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, c * nkg, nkg, sA, sh.a_plane, sbo);
+        }
         tc::fence_smem_async();
         tc::fence_before();
         __syncthreads();

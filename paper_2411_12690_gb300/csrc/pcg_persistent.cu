@@ -280,8 +280,10 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         // ---- phase B: interface sum, <p, q>, alpha
         {
             ArrayCursor cur{-1, 0};
+            VecWork next = blockIdx.x < a.n_vwork ? a.vwork[blockIdx.x] : VecWork{};
             for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
-                const VecWork it = a.vwork[w];
+                const VecWork it = next;
+                if (w + (int)gridDim.x < a.n_vwork) next = a.vwork[w + gridDim.x];   // overlaps this item
                 if (it.array != cur.k) switch_array(cur, it.array, 1);
                 if (!s_active) continue;
                 const V acc = pi::isum_item<4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
@@ -297,12 +299,14 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         // ---- phase C: vector update, <r,z>, <r,r>, beta, stopping test
         {
             ArrayCursor cur{-1, 0};
+            VecWork next = blockIdx.x < a.n_vwork ? a.vwork[blockIdx.x] : VecWork{};
             for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
-                const VecWork it = a.vwork[w];
+                const VecWork it = next;
+                if (w + (int)gridDim.x < a.n_vwork) next = a.vwork[w + gridDim.x];
                 if (it.array != cur.k) switch_array(cur, it.array, 2);
                 if (!s_active) continue;
                 V srz, srr;
-                pi::vec1_item<4, V>(it, static_cast<const V*>(a.dinv), (V)s_scalar, x, r, z, p, q, srz, srr);
+                pi::vec1_item<NT >= 512 ? 8 : 4, V>(it, static_cast<const V*>(a.dinv), (V)s_scalar, x, r, z, p, q, srz, srr);
                 const double rz = pi::block_sum(srz, shr);
                 const double rr = pi::block_sum(srr, shr);
                 if (tid == 0) {

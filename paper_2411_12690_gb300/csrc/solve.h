@@ -6,7 +6,11 @@
 
 namespace ms {
 
-constexpr int kVecChunk = 2048;   // lattice DOFs per vector work item
+// Lattice DOFs per vector work item: FP64 solves 2048 (256 threads x 2 rounds
+// of 4), reduced-precision solves 4096 (512 threads x 8). The chunking is a
+// function of the array and the precision only, never of the batch.
+constexpr int kVecChunk64 = 2048;
+constexpr int kVecChunk32 = 4096;
 constexpr int kTile64 = 32;       // blocks per CUDA-core apply / recovery tile
 constexpr int kTileTC = 128;      // blocks per tensor-core apply tile (the MMA M dimension)
 
@@ -91,6 +95,7 @@ struct mstress_sol_s {
     void* Y64 = nullptr;                  // FP64 element products (Y64own, or Y in FP64 mode)
     ms::DBuf Y;                           // element-by-element products [block][ldY]
     ms::DBuf part;                        // 3 * n_vwork partial sums
+    ms::DBuf cimg;                        // coefficient images of the tensor-core recovery (reused)
     ms::DBuf flag;                        // device ints: [0] any active, [1] CTA ticket, [2] error,
                                           // [3] loop count, [4] arrays active, [7] abort
     ms::DBuf tickets;                     // 2 ints per array (persistent solver folds)

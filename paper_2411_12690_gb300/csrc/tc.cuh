@@ -85,16 +85,30 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
 }
 
 // Wait for the given phase parity of an mbarrier, giving up after max_tries
-// polls (each try_wait may itself suspend briefly). Returns false on timeout.
+// polls (each try_wait may itself suspend briefly) or about two seconds,
+// whichever comes first. Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int max_tries) {
     uint32_t done = 0;
-    for (int it = 0; it < max_tries && !done; ++it)
+    unsigned long long t0 = 0;
+    for (int it = 0; it < max_tries && !done; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
             : "r"(smem_addr(mbar)), "r"(parity)
             : "memory");
+        if ((it & 1023) == 1023 && !done) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 2000000000ull) break;
+        }
+    }
     return done != 0;
+}
+
+// Plain arrive (one of the barrier's expected arrivals).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
 
 // Arrive on the mbarrier and raise its expected transaction count by bytes.

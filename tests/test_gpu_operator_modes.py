@@ -95,3 +95,25 @@ def test_refinement_m294_reaches_fp64_accuracy(api, mode):
     if mode == L.MSTRESS_BF16X3:
         assert rel_l2(vm, ovm) <= 1e-4
 
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_recovery_m168_within_rounding_bound(api, mode):
+    """Per-element von Mises at m = 168 (a larger tensor-core recovery tile:
+    one S_mean stage next to the coefficients in the split modes) against the
+    oracle, within the per-element rounding bound of the recovery."""
+    from test_gpu_mixed import vm_bound
+    spec = SPECS[3]
+    ctx = api.Context(precision=mode)
+    blks = [ctx.build_block(spec), ctx.build_block(spec.dummy())]
+    st = W.site_types(13, 11, 0.75, seed=9)       # 143 blocks: two 128-block recovery tiles
+    sol = ctx.solve(st, blks, -200.0)
+    assert sol.info()["status"] == 0
+    ob, osol = oracle_solve(spec, st, -200.0)
+    n_el = spec.ex * spec.ey * spec.ez
+    vm = sol.recover(L.MSTRESS_VM_ELEM).reshape(-1, n_el)
+    ovm = mor.recover_vm(ob, osol)
+    bound = vm_bound(ob, osol, mode)
+    err = np.abs(vm.astype(np.float64) - ovm)
+    print(f"mode {mode}: vm relL2 {rel_l2(vm, ovm):.2e} max err/bound {np.max(err / bound):.3f}")
+    assert np.all(err <= bound + 1e-12 * ovm.max())
