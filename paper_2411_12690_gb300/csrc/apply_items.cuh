@@ -183,14 +183,9 @@ __device__ __forceinline__ void put_operand(uint8_t* plane0, uint32_t plane_byte
 
 __device__ __forceinline__ void put_operand(uint8_t* plane0, uint32_t plane_bytes, uint32_t off, float v, int mode);
 
-// Gather K groups [kg0, kg0 + nkg) of a tile's coefficients into a K-major
-// no-swizzle operand (K group = 16 bytes of K: 8 bf16 or 4 tf32 values; local
-// group kgl of the destination at kgl * 128 bytes, row groups sbo apart). The
-// thread mapping follows the core matrices: consecutive threads take
-// consecutive K values of one row, then the next rows, so a warp's stores fill
-// contiguous shared memory (no bank conflicts) and its loads run along a
-// block's contiguous lattice DOFs. Rows [count, 1 << lg_tile) and columns
-// >= m are written as zeros. Eight values per thread are in flight at a time.
+// Element idx of a gathered range of 16-byte K groups of a tile: consecutive
+// indices take consecutive K values of one row, then the rows of the tile,
+// then the K groups.
 template <int MODE>
 struct OperandMap {   // element idx of a gathered K-group range -> (row, column, shared-memory offset)
     static constexpr int ESZ = MODE == MSTRESS_TF32 ? 4 : 2;
@@ -339,11 +334,21 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
 // Large bases (m > 80): K_r does not fit in shared memory next to the
 // coefficient tile, so both operands move through `stages` ring slots of ck
 // K-elements each (two MMA K steps). Slot c of the operator image is one
-// contiguous block in global memory, fetched with a single bulk copy that runs
-// while the CTA gathers the matching coefficient columns. An mbarrier per slot
-// counts the copy's bytes (full); a tcgen05.commit per slot frees it once
-// its MMAs are done (empty). N (= m padded to 16) is split into MMAs of at
-// most 256 columns; the accumulator takes npad TMEM columns.
+// contiguous block in global memory, fetched with a single bulk copy. N (= m
+// padded to 16) is split into MMAs of at most 256 columns; the accumulator
+// takes npad TMEM columns.
+//
+// The CTA is warp-specialised (kTcsThreads = 16 warps):
+//   warp 0, lane 0   issues the operator copies and the MMAs;
+//   warps 1..4       epilogue: TMEM lanes 32 (w % 4) .. +31 = the tile's
+//                    blocks, all npad columns, written to Y;
+//   warps 5..15      gather the coefficients of each K slot (352 threads).
+// mbarriers per ring slot: fullA (the 352 gather threads arrive), fullB (the
+// operator copy's bytes), empty (tcgen05.commit once the slot's MMAs are
+// done); per CTA: accF (commit after a tile's last MMAs) and accE (the 128
+// epilogue threads arrive when the accumulator has been read). Gather,
+// operator copies, MMAs and the epilogue of consecutive slots and tiles
+// overlap; every wait is bounded and a failure stops all roles.
 struct TcsShape {
     int m, esz, ns, ck, nck, kpad, npad, n0, n1, tmem_cols, stages;
     int lg_tile;                 // log2 of the blocks per tile of the solve (rows gathered per tile)
@@ -352,134 +357,322 @@ struct TcsShape {
     size_t smem;
 };
 
-struct TcsState {
-    uint8_t* slots;        // stages x (A slot | B slot)
-    uint64_t* full;        // [stages] operator copy landed
-    uint64_t* empty;       // [stages] MMAs reading the slot are done
-    uint32_t tmem;
-    uint32_t chunk;        // slots used so far by this CTA (sets slot and parity)
-};
-
 }  // namespace ai
 
 ai::TcsShape tcs_shape(int m, int prec);   // streamed tensor-core apply geometry (tc.cu)
 
 namespace ai {
 
-// D (128 x npad) = C (tile blocks x K) * K_r^T for one tile, K streamed.
-// Returns false if a wait timed out (the caller stops and reports it).
+constexpr int kTcsThreads = 512;       // 16 warps
+constexpr int kTcsEpi0 = 32, kTcsEpi = 128;        // epilogue threads [32, 160)
+constexpr int kTcsGather0 = 160, kTcsGather = 352; // gather threads [160, 512)
+constexpr int kTcsQU = 3;              // gather units per thread per slot (352 x 3 >= 1024 units of 4 values)
+
+struct TcsState {
+    uint8_t* slots;        // stages x (A slot | B slot)
+    uint64_t *fullA, *fullB, *empty, *accF, *accE;
+    uint32_t tmem;
+    uint32_t chunk;        // K slots used so far by this CTA (sets slot and parity)
+    uint32_t tiles;        // tiles accumulated so far by this CTA (sets accumulator parity)
+    int* fail;             // shared: a wait expired
+};
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads, so
+// that they all take the same branch afterwards.
+__device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// Per-tile gather set-up by the gather threads only (thread t of n).
+__device__ __forceinline__ void tile_setup_part(const ApplyArgs& a, const ApplyWork& it, const ArrayDev& A,
+                                                long long* base, int* offs, int t, int n) {
+    const int n1 = a.lm->n - 1;
+    for (int k = t; k < a.m; k += n) {
+        const int q = k / 3, c = k - 3 * q;
+        offs[k] = ((a.lm->qc[q] * A.Y + a.lm->qb[q]) * A.X + a.lm->qa[q]) * 3 + c;
+    }
+    for (int b = t; b < it.count; b += n) {
+        const BlockRef br = a.bref[a.blist[it.start + b]];
+        base[b] = A.vec_off + 3LL * ((long long)br.j * n1 * A.X + (long long)br.i * n1);
+    }
+}
+
+// Gather of one K slot (4 groups of 16 bytes of K) of a tile in quads: a
+// gather unit is 4 consecutive K values of one row, so each unit costs one
+// base and one 16-byte offset lookup, eight global loads and one store per
+// operand plane (8 bytes of bf16 or 16 bytes of tf32). Consecutive units run
+// over the 8 rows of a core matrix, then its halves (bf16), then the K groups
+// and the row groups, so a warp's stores cover whole core matrices.
 template <int MODE>
-__device__ __forceinline__ bool apply_tcs_item(const ApplyArgs& a, const TcsShape& sh, const ApplyWork& it,
-                                               TcsState& ts, long long* base, int* offs) {
-    constexpr bool TF32 = MODE == MSTRESS_TF32;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x, nw = nt >> 5;
-    const int m = a.m;
-    const ArrayDev A = a.arrays[it.array];
-    const float beta = a.st ? (float)a.st[it.array].beta : 0.f;
-    const float* __restrict__ x = static_cast<const float*>(a.x);
-    const float* __restrict__ z = static_cast<const float*>(a.z);
-    float* __restrict__ Y = static_cast<float*>(a.Y);
-    const uint8_t* img = static_cast<const uint8_t*>(a.tt.Klp[it.type]);
-    tile_setup(a, it, A, base, offs, kTileTC);
-    __syncthreads();
-    const uint32_t sbo = tc::sbo_bytes(sh.ck, sh.esz);
-    const uint32_t slot_bytes = sh.a_stage + sh.b_stage;
-    bool ok = true;
-    uint32_t last = 0;
-    // When a chunk is one round of loads (blockDim.x * 8 >= its values), the
-    // values of chunk c + 1 are loaded into registers while chunk c is stored
-    // and its MMAs are issued, so one load latency overlaps the next.
-    constexpr int GU = 8;
-    const int nkg = sh.ck * sh.esz / 16;
-    const int total = nkg << (sh.lg_tile + OperandMap<MODE>::LGKE);
-    const bool one_round = total <= nt * GU;
-    float vcur[GU], vnext[GU];
-    if (one_round) operand_load<MODE, GU>(x, z, beta, m, it.count, base, offs, sh.lg_tile, 0, total, tid, vcur);
-    for (int c = 0; c < sh.nck; ++c) {
-        const uint32_t g = ts.chunk++, slot = g % (uint32_t)sh.stages, use = g / (uint32_t)sh.stages;
-        uint8_t* sA = ts.slots + slot * slot_bytes;
-        uint8_t* sB = sA + sh.a_stage;
-        last = g;
-        if (use > 0 && ok) ok = tc::mbar_wait(&ts.empty[slot], (use - 1) & 1u, 1 << 24);
-        if (__syncthreads_or(!ok)) return false;
-        if (tid == 0) {
-            tc::mbar_expect_tx(&ts.full[slot], sh.b_stage);
-            tc::bulk_g2s(sB, img + (size_t)c * sh.b_stage, sh.b_stage, &ts.full[slot]);
-        }
-        if (one_round) {
-            if (c + 1 < sh.nck)
-                operand_load<MODE, GU>(x, z, beta, m, it.count, base, offs, sh.lg_tile, (c + 1) * nkg, total, tid,
-                                       vnext);
-            operand_store<MODE, GU>(sh.lg_tile, total, tid, vcur, sA, sh.a_plane, sbo);
+struct QuadMap {
+    static constexpr int LGHQ = MODE == MSTRESS_TF32 ? 0 : 1;   // log2 of quads per 16-byte K group
+    static constexpr int UNITS = 128 * 4 << LGHQ;               // units of a 128-row slot
+    __device__ __forceinline__ static int row(int ui) { return ((ui >> (5 + LGHQ)) << 3) + (ui & 7); }
+    __device__ __forceinline__ static int kg(int ui) { return (ui >> (3 + LGHQ)) & 3; }
+    __device__ __forceinline__ static int col(int ui) {   // first K value of the unit within the slot
+        return (kg(ui) << (2 + LGHQ)) + (((ui >> 3) & ((1 << LGHQ) - 1)) << 2);
+    }
+    __device__ __forceinline__ static uint32_t off(int ui, uint32_t sbo) {
+        return (uint32_t)(ui >> (5 + LGHQ)) * sbo + (uint32_t)kg(ui) * 128u + (uint32_t)(ui & 7) * 16u +
+               (uint32_t)((ui >> 3) & ((1 << LGHQ) - 1)) * 8u;
+    }
+};
+
+template <int MODE, int QU>
+__device__ __forceinline__ void quad_load(const float* __restrict__ x, const float* __restrict__ z, float beta, int m,
+                                          int count, const long long* base, const int* offs, int k0, int u0, int nthr,
+                                          float (&v)[QU][4]) {
+    using QM = QuadMap<MODE>;
 #pragma unroll
-            for (int u = 0; u < GU; ++u) vcur[u] = vnext[u];
+    for (int q = 0; q < QU; ++q) {
+        const int ui = u0 + q * nthr;
+        const int b = QM::row(ui), k = k0 + QM::col(ui);
+        const bool live = ui < QM::UNITS && b < count;
+        long long bb = 0;
+        int4 o = make_int4(0, 0, 0, 0);
+        if (live) {
+            bb = base[b];
+            if (k + 3 < m) o = *reinterpret_cast<const int4*>(offs + k);
+            else {
+                o.x = k < m ? offs[k] : 0;
+                o.y = k + 1 < m ? offs[k + 1] : 0;
+                o.z = k + 2 < m ? offs[k + 2] : 0;
+            }
+        }
+        v[q][0] = live && k < m ? gather(x, z, bb + o.x, beta) : 0.f;
+        v[q][1] = live && k + 1 < m ? gather(x, z, bb + o.y, beta) : 0.f;
+        v[q][2] = live && k + 2 < m ? gather(x, z, bb + o.z, beta) : 0.f;
+        v[q][3] = live && k + 3 < m ? gather(x, z, bb + o.w, beta) : 0.f;
+    }
+}
+
+template <int MODE, int QU>
+__device__ __forceinline__ void quad_store(int u0, int nthr, const float (&v)[QU][4], uint8_t* plane0,
+                                           uint32_t plane_bytes, uint32_t sbo) {
+    using QM = QuadMap<MODE>;
+#pragma unroll
+    for (int q = 0; q < QU; ++q) {
+        const int ui = u0 + q * nthr;
+        if (ui >= QM::UNITS) continue;
+        uint8_t* dst = plane0 + QM::off(ui, sbo);
+        if (MODE == MSTRESS_TF32) {
+            *reinterpret_cast<float4*>(dst) =
+                make_float4(tc::to_tf32(v[q][0]), tc::to_tf32(v[q][1]), tc::to_tf32(v[q][2]), tc::to_tf32(v[q][3]));
         } else {
-            gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, c * nkg, nkg, sA, sh.a_plane, sbo);
-        }
-        tc::fence_smem_async();
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-        if (tid == 0) {
-            ok = tc::mbar_wait(&ts.full[slot], use & 1u, 1 << 24);
-            if (ok) {
-                const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-                const uint32_t id0 = tc::instr_desc(TF32, kTileTC, sh.n0);
-                const uint32_t id1 = tc::instr_desc(TF32, kTileTC, sh.n1 > 0 ? sh.n1 : 16);
-                const uint32_t b1 = (uint32_t)(sh.n0 >> 3) * sbo;   // row n0 of the operator slot
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const uint32_t ko = (uint32_t)j * 2 * tc::kLBO;
-                    // products (A plane, B plane): (hi, hi) [, (lo, hi), (hi, lo)]
-#pragma unroll
-                    for (int pr = 0; pr < (MODE == MSTRESS_BF16X3 ? 3 : 1); ++pr) {
-                        const uint32_t pa = pr == 1 ? sh.a_plane : 0u, pb = pr == 2 ? sh.b_plane : 0u;
-                        const uint32_t acc = (c > 0 || j > 0 || pr > 0) ? 1u : 0u;
-                        const uint64_t da = tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo);
-                        tc::mma<TF32>(ts.tmem, da, tc::smem_desc(b0 + pb + ko, tc::kLBO, sbo), id0, acc);
-                        if (sh.n1 > 0)
-                            tc::mma<TF32>(ts.tmem + (uint32_t)sh.n0, da,
-                                          tc::smem_desc(b0 + pb + b1 + ko, tc::kLBO, sbo), id1, acc);
-                    }
-                }
-                tc::commit(&ts.empty[slot]);
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[q][0], v[q][1]), h1 = __floats2bfloat162_rn(v[q][2], v[q][3]);
+            uint2 hw;
+            hw.x = *reinterpret_cast<uint32_t*>(&h0);
+            hw.y = *reinterpret_cast<uint32_t*>(&h1);
+            *reinterpret_cast<uint2*>(dst) = hw;
+            if (MODE == MSTRESS_BF16X3) {
+                const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+                __nv_bfloat162 l0 = __floats2bfloat162_rn(v[q][0] - f0.x, v[q][1] - f0.y);
+                __nv_bfloat162 l1 = __floats2bfloat162_rn(v[q][2] - f1.x, v[q][3] - f1.y);
+                uint2 lw;
+                lw.x = *reinterpret_cast<uint32_t*>(&l0);
+                lw.y = *reinterpret_cast<uint32_t*>(&l1);
+                *reinterpret_cast<uint2*>(dst + plane_bytes) = lw;
             }
         }
     }
-    if (__syncthreads_or(!ok)) return false;
-    // all MMAs of the tile are done once the last slot's commit has arrived
-    ok = tc::mbar_wait(&ts.empty[last % (uint32_t)sh.stages], (last / (uint32_t)sh.stages) & 1u, 1 << 24);
-    tc::fence_after();
-    if (__syncthreads_or(!ok)) return false;
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one block each) and
-    // column chunks 16 (w / 4), 16 (w / 4 + nw / 4), ...
-    const int b = (warp & 3) * 32 + lane;
-    const long long e = b < it.count ? a.blist[it.start + b] : 0;
-    for (int c0 = 16 * (warp >> 2); c0 < sh.npad; c0 += 16 * (nw >> 2)) {
-        float v[16];
-        tc::tmem_ld16(ts.tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
-        if (b < it.count) {
-            float4* dst = reinterpret_cast<float4*>(Y + e * a.ldY + c0);
-            dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-            dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-            dst[2] = make_float4(v[8], v[9], v[10], v[11]);
-            dst[3] = make_float4(v[12], v[13], v[14], v[15]);
-        }
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    return true;
 }
 
-// Set up the slot barriers of a streamed tensor-core CTA (all threads call).
-__device__ __forceinline__ void tcs_init(TcsState& ts, const TcsShape& sh, uint8_t* smem, uint64_t* bars) {
+// The tiles w0, w0 + wstride, ... (< a.n_work) of arrays still active: every
+// thread of the CTA calls this; each takes its role. Returns false if a wait
+// expired (ts.fail set). PREFETCH: the gather loads the next K slot's values
+// while it stores the current one (two register sets); without it (a kernel
+// with less register room) one set.
+template <int MODE, bool PREFETCH = true>
+__device__ bool tcs_apply_phase(const ApplyArgs& a, const TcsShape& sh, TcsState& ts, long long* base, int* offs,
+                                int w0, int wstride) {
+    constexpr bool TF32 = MODE == MSTRESS_TF32;
+    constexpr int kTries = 1 << 24;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t S = (uint32_t)sh.stages;
+    const uint32_t slot_bytes = sh.a_stage + sh.b_stage;
+    const uint32_t sbo = tc::sbo_bytes(sh.ck, sh.esz);
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    const float* __restrict__ z = static_cast<const float*>(a.z);
+    float* __restrict__ Y = static_cast<float*>(a.Y);
+    uint32_t g = ts.chunk, tt = ts.tiles;
+    int* fail = ts.fail;
+    if (warp == 0) {
+        // ---------------- operator copies and MMAs
+        if (lane == 0) {
+            const uint32_t id0 = tc::instr_desc(TF32, kTileTC, sh.n0);
+            const uint32_t id1 = tc::instr_desc(TF32, kTileTC, sh.n1 > 0 ? sh.n1 : 16);
+            const uint32_t b1 = (uint32_t)(sh.n0 >> 3) * sbo;   // row n0 of an operator slot
+            for (int w = w0; w < a.n_work && !*(volatile int*)fail; w += wstride) {
+                const ApplyWork it = a.work[w];
+                if (a.st && !__ldcg(&a.st[it.array].active)) continue;
+                const uint8_t* img = static_cast<const uint8_t*>(a.tt.Klp[it.type]);
+                bool ok = true;
+                // operator slots of the tile's first chunks (their previous MMAs must be done)
+                for (uint32_t i = 0; i < S && (int)i < sh.nck && ok; ++i) {
+                    const uint32_t gi = g + i, si = gi % S, ui = gi / S;
+                    if (ui > 0) ok = tc::mbar_wait(&ts.empty[si], (ui - 1) & 1u, kTries);
+                    if (ok) {
+                        tc::mbar_expect_tx(&ts.fullB[si], sh.b_stage);
+                        tc::bulk_g2s(ts.slots + si * slot_bytes + sh.a_stage, img + (size_t)i * sh.b_stage,
+                                     sh.b_stage, &ts.fullB[si]);
+                    }
+                }
+                // the accumulator is free once the previous tile's epilogue has read it
+                if (ok && tt > 0) ok = tc::mbar_wait(ts.accE, (tt - 1) & 1u, kTries);
+                for (int c = 0; c < sh.nck && ok; ++c, ++g) {
+                    const uint32_t slot = g % S, use = g / S;
+                    ok = tc::mbar_wait(&ts.fullA[slot], use & 1u, kTries) &&
+                         tc::mbar_wait(&ts.fullB[slot], use & 1u, kTries);
+                    tc::fence_after();
+                    if (!ok) break;
+                    const uint32_t a0 = tc::smem_addr(ts.slots + slot * slot_bytes);
+                    const uint32_t bb0 = a0 + sh.a_stage;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t ko = (uint32_t)j * 2 * tc::kLBO;
+                        // products (A plane, B plane): (hi, hi) [, (lo, hi), (hi, lo)]
+#pragma unroll
+                        for (int pr = 0; pr < (MODE == MSTRESS_BF16X3 ? 3 : 1); ++pr) {
+                            const uint32_t pa = pr == 1 ? sh.a_plane : 0u, pb = pr == 2 ? sh.b_plane : 0u;
+                            const uint32_t acc = (c > 0 || j > 0 || pr > 0) ? 1u : 0u;
+                            const uint64_t da = tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo);
+                            tc::mma<TF32>(ts.tmem, da, tc::smem_desc(bb0 + pb + ko, tc::kLBO, sbo), id0, acc);
+                            if (sh.n1 > 0)
+                                tc::mma<TF32>(ts.tmem + (uint32_t)sh.n0, da,
+                                              tc::smem_desc(bb0 + pb + b1 + ko, tc::kLBO, sbo), id1, acc);
+                        }
+                    }
+                    tc::commit(&ts.empty[slot]);
+                    if (c == sh.nck - 1) {
+                        tc::commit(ts.accF);
+                    } else if (c >= 1 && c - 1 + (int)S < sh.nck) {
+                        // refill the previous chunk's operator slot once its MMAs are done
+                        const uint32_t gp = g - 1, sp = gp % S;
+                        ok = tc::mbar_wait(&ts.empty[sp], (gp / S) & 1u, kTries);
+                        if (ok) {
+                            tc::mbar_expect_tx(&ts.fullB[sp], sh.b_stage);
+                            tc::bulk_g2s(ts.slots + sp * slot_bytes + sh.a_stage,
+                                         img + (size_t)(c - 1 + S) * sh.b_stage, sh.b_stage, &ts.fullB[sp]);
+                        }
+                    }
+                }
+                if (!ok) {
+                    *(volatile int*)fail = 1;
+                    break;
+                }
+                ++tt;
+            }
+        }
+    } else if (warp < 5) {
+        // ---------------- epilogue: accumulator lanes -> element products Y
+        const int b = ((warp & 3) << 5) + lane;
+        for (int w = w0; w < a.n_work; w += wstride) {
+            const ApplyWork it = a.work[w];
+            if (a.st && !__ldcg(&a.st[it.array].active)) continue;
+            bool ok = !*(volatile int*)fail && tc::mbar_wait(ts.accF, tt & 1u, kTries);
+            tc::fence_after();
+            if (!ok) {
+                *(volatile int*)fail = 1;
+                break;
+            }
+            const long long e = b < it.count ? a.blist[it.start + b] : -1;
+            const uint32_t tl = ts.tmem + ((uint32_t)((warp & 3) << 5) << 16);
+            for (int c0 = 0; c0 < sh.npad; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tl + (uint32_t)c0, v);
+                if (e >= 0) {
+                    float4* dst = reinterpret_cast<float4*>(Y + e * a.ldY + c0);
+                    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+                    dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+                }
+            }
+            tc::fence_before();
+            tc::mbar_arrive(ts.accE);
+            ++tt;
+        }
+    } else {
+        // ---------------- gather of the coefficient slots
+        const int gt = tid - kTcsGather0;
+        for (int w = w0; w < a.n_work; w += wstride) {
+            const ApplyWork it = a.work[w];
+            if (a.st && !__ldcg(&a.st[it.array].active)) continue;
+            // the previous tile's gather is done with base / offs; every gather
+            // thread takes the same decision to stop (a named barrier must not
+            // be left with missing arrivals)
+            if (named_sync_or(1, kTcsGather, *(volatile int*)fail != 0)) break;
+            const ArrayDev A = a.arrays[it.array];
+            const float beta = a.st ? (float)a.st[it.array].beta : 0.f;
+            tile_setup_part(a, it, A, base, offs, gt, kTcsGather);
+            named_sync(1, kTcsGather);
+            float vc[kTcsQU][4], vn[kTcsQU][4];
+            if (PREFETCH) quad_load<MODE, kTcsQU>(x, z, beta, a.m, it.count, base, offs, 0, gt, kTcsGather, vc);
+            bool ok = true;
+            for (int c = 0; c < sh.nck; ++c, ++g) {
+                const uint32_t slot = g % S, use = g / S;
+                if (!PREFETCH)   // loads issued before the wait for the slot, so they overlap it
+                    quad_load<MODE, kTcsQU>(x, z, beta, a.m, it.count, base, offs, c * sh.ck, gt, kTcsGather, vc);
+                if (use > 0) ok = tc::mbar_wait(&ts.empty[slot], (use - 1) & 1u, kTries);
+                if (!ok) break;
+                if (PREFETCH && c + 1 < sh.nck)   // next slot's values in flight while this one is stored
+                    quad_load<MODE, kTcsQU>(x, z, beta, a.m, it.count, base, offs, (c + 1) * sh.ck, gt, kTcsGather,
+                                            vn);
+                quad_store<MODE, kTcsQU>(gt, kTcsGather, vc, ts.slots + slot * slot_bytes, sh.a_plane, sbo);
+                tc::fence_smem_async();
+                tc::mbar_arrive(&ts.fullA[slot]);
+                if (PREFETCH) {
+#pragma unroll
+                    for (int q = 0; q < kTcsQU; ++q)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) vc[q][j] = vn[q][j];
+                }
+            }
+            if (!ok) *(volatile int*)fail = 1;   // all gather threads stop at the next tile's barrier
+        }
+    }
+    __syncthreads();
+    // every role counted the same active tiles
+    uint32_t n_tiles = 0;
+    for (int w = w0; w < a.n_work; w += wstride)
+        if (!a.st || __ldcg(&a.st[a.work[w].array].active)) ++n_tiles;
+    ts.chunk += n_tiles * (uint32_t)sh.nck;
+    ts.tiles += n_tiles;
+    return *(volatile int*)fail == 0;
+}
+
+// Set up the barriers and zero the gathered-operand slots of a streamed
+// tensor-core CTA (all threads call; the caller synchronises afterwards).
+__device__ __forceinline__ void tcs_init(TcsState& ts, const TcsShape& sh, uint8_t* smem, uint64_t* bars, int* fail) {
     ts.slots = smem;
-    ts.full = bars;
-    ts.empty = bars + sh.stages;
+    ts.fullA = bars;
+    ts.fullB = bars + sh.stages;
+    ts.empty = bars + 2 * sh.stages;
+    ts.accF = bars + 3 * sh.stages;
+    ts.accE = ts.accF + 1;
     ts.chunk = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < 2 * sh.stages; ++i) tc::mbar_init(&bars[i], 1);
+    ts.tiles = 0;
+    ts.fail = fail;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < sh.stages; ++i) {
+            tc::mbar_init(&ts.fullA[i], kTcsGather);
+            tc::mbar_init(&ts.fullB[i], 1);
+            tc::mbar_init(&ts.empty[i], 1);
+        }
+        tc::mbar_init(ts.accF, 1);
+        tc::mbar_init(ts.accE, kTcsEpi);
+        *fail = 0;
+    }
     // rows at or beyond the solve's tile size are never gathered: keep them zero
     for (int st = 0; st < sh.stages; ++st) {
         uint4* a0 = reinterpret_cast<uint4*>(smem + (size_t)st * (sh.a_stage + sh.b_stage));
@@ -491,13 +684,14 @@ __device__ __forceinline__ void tcs_init(TcsState& ts, const TcsShape& sh, uint8
 // let outstanding operator copies and MMAs finish so that neither writes
 // shared or tensor memory after the CTA is gone.
 __device__ __forceinline__ void tcs_drain(const TcsState& ts, const TcsShape& sh) {
-    if (threadIdx.x != 0 || ts.chunk == 0) return;
-    const uint32_t n = ts.chunk < (uint32_t)sh.stages ? ts.chunk : (uint32_t)sh.stages;
-    for (uint32_t i = 0; i < n; ++i) {
-        const uint32_t g = ts.chunk - 1 - i, slot = g % (uint32_t)sh.stages, use = g / (uint32_t)sh.stages;
-        tc::mbar_wait(&ts.full[slot], use & 1u, 1 << 20);
-        tc::mbar_wait(&ts.empty[slot], use & 1u, 1 << 20);
-    }
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < sh.stages; ++i)
+        for (uint32_t par = 0; par < 2; ++par) {
+            tc::mbar_wait(&ts.fullB[i], par, 1 << 16);
+            tc::mbar_wait(&ts.empty[i], par, 1 << 16);
+        }
+    tc::mbar_wait(ts.accF, 0, 1 << 16);
+    tc::mbar_wait(ts.accF, 1, 1 << 16);
 }
 
 }  // namespace ai

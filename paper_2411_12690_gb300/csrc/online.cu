@@ -22,9 +22,10 @@
 // which keeps r, z, p zero there; prescribed values enter b by lifting (Eq. 13).
 //
 // Precision: FP64 vectors and FP64 operator in the plain mode; in the mixed
-// modes an FP64 outer loop (residual b - A x with the FP64 operator, a5)
-// drives an inner PCG with FP32 vectors and a reduced-precision operator, while
-// all dot products and step lengths stay FP64.
+// modes an FP64 outer loop (residual b - A x with the FP64 operator)
+// drives an inner PCG with FP32 vectors and a reduced-precision operator; the
+// inner dot products are per-thread FP32 partial sums folded in FP64, and the
+// step lengths are FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -545,7 +546,7 @@ void pcg_iteration(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond, cuda
     constexpr bool f32 = std::is_same<V, float>::value;
     cudaStream_t stream = s->ctx->stream;
     const PcgState* st = v.state.as<PcgState>();
-    launch_apply(s, prec, v.p.ptr, v.z.ptr, f32, st, s->Y.ptr);
+    launch_apply(s, prec, v.p.ptr, v.z.ptr, f32, st, s->Y.ptr);   // gathers p = z + beta p
     launch_isum(s, s->Y.ptr, f32, v.p.ptr, v.z.ptr, v.q.ptr, f32, f32 ? s->dinv32.ptr : s->dinv.ptr, st,
                 s->part.as<double>());
     VecArgs va = vec_args(s, v);

@@ -109,9 +109,10 @@ __device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __r
 }
 
 // Interface sum of one vector work item: q_g = sum of Y_e over the owning
-// blocks (fixed order), p updated to z + beta p when z is given; returns this
-// thread's share of <p, q>. Arithmetic in the vector precision V (dinv, the
-// constrained-row mask, in V as well).
+// blocks (fixed order), p updated to z + beta p when z is given (the apply
+// gathered the same p_e with the same arithmetic); returns this thread's share
+// of <p, q>. Arithmetic in the vector precision V (dinv, the constrained-row
+// mask, in V as well).
 // Each thread handles U DOFs at once and issues all their loads (mask,
 // direction, up to four owner contributions) before combining, so a work item
 // of U * blockDim.x DOFs costs one round trip to L2 instead of a chain of

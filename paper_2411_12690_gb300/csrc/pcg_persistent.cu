@@ -126,20 +126,21 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ long long base[kTileTC];
-    __shared__ int offs[3 * kMaxSurf];
+    __shared__ __align__(16) int offs[3 * kMaxSurf];
     __shared__ double shr[NT / 32], sh8[8];
     __shared__ int s_flag, s_ok, s_active;
     __shared__ double s_scalar;
     __shared__ ArrayDev s_A;
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ __align__(8) uint64_t bars[8];
+    __shared__ __align__(8) uint64_t bars[3 * 4 + 2];
+    __shared__ int s_tcs_fail;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x;
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
     ai::TcState ts;
     ai::TcsState tss;
     if constexpr (AM == AM_TCS) {
-        ai::tcs_init(tss, a.shs, smem, bars);
+        ai::tcs_init(tss, a.shs, smem, bars, &s_tcs_fail);
         if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.shs.tmem_cols);
         tc::fence_before();
         __syncthreads();
@@ -252,12 +253,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                     break;
                 }
             } else if constexpr (AM == AM_TCS) {
-                const ApplyWork it = a.ap.work[w];
-                if (!__ldcg(&a.st[it.array].active)) continue;
-                if (!ai::apply_tcs_item<MODE>(a.ap, a.shs, it, tss, base, offs)) {
-                    failed = true;
-                    break;
-                }
+                break;   // the warp-specialised phase below takes all of the CTA's tiles
             } else {
                 const ApplyWork it = a.ap.work[w / a.panels];
                 if (!__ldcg(&a.st[it.array].active)) continue;
@@ -271,6 +267,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                                                 offs);
             }
         }
+        if constexpr (AM == AM_TCS) failed = !ai::tcs_apply_phase<MODE, false>(a.ap, a.shs, tss, base, offs, blockIdx.x,
+                                                                         gridDim.x);
         if (failed && tid == 0) {
             atomicExch(a.err, 1);
             atomicExch(a.abort, 1);
@@ -286,7 +284,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 if (w + (int)gridDim.x < a.n_vwork) next = a.vwork[w + gridDim.x];   // overlaps this item
                 if (it.array != cur.k) switch_array(cur, it.array, 1);
                 if (!s_active) continue;
-                const V acc = pi::isum_item<4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
+                const V acc = pi::isum_item<sizeof(V) == 8 ? 2 : 4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
                                                      static_cast<const V*>(a.ap.Y), p, z, q, (V)s_scalar);
                 const double t = pi::block_sum(acc, shr);
                 if (tid == 0) a.part_pq[w] = t;
@@ -363,7 +361,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     PcgArgs a;
     std::memset(&a, 0, sizeof(a));
     const bool tc = vec_fp32 && s->use_tc;
-    a.ap = apply_args(s, v.p.ptr, v.z.ptr, v.state.as<PcgState>(), s->Y.ptr, tc);
+    a.ap = apply_args(s, v.p.ptr, v.z.ptr, v.state.as<PcgState>(), s->Y.ptr, tc);   // gathers p = z + beta p
     a.vwork = s->d_vwork.as<VecWork>();
     a.n_vwork = s->n_vwork;
     a.arrays = s->d_arrays.as<ArrayDev>();
@@ -415,11 +413,11 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
         const int tm = a.shs.tmem_cols;
         switch (prec) {
             case MSTRESS_TF32:
-                return launch_coop<512>(k_pcg<float, AM_TCS, MSTRESS_TF32, 0, 512, 1>, s, a, a.shs.smem, need, tm);
+                return launch_coop<ai::kTcsThreads>(k_pcg<float, AM_TCS, MSTRESS_TF32, 0, ai::kTcsThreads, 1>, s, a, a.shs.smem, need, tm);
             case MSTRESS_BF16:
-                return launch_coop<512>(k_pcg<float, AM_TCS, MSTRESS_BF16, 0, 512, 1>, s, a, a.shs.smem, need, tm);
+                return launch_coop<ai::kTcsThreads>(k_pcg<float, AM_TCS, MSTRESS_BF16, 0, ai::kTcsThreads, 1>, s, a, a.shs.smem, need, tm);
             default:
-                return launch_coop<512>(k_pcg<float, AM_TCS, MSTRESS_BF16X3, 0, 512, 1>, s, a, a.shs.smem, need, tm);
+                return launch_coop<ai::kTcsThreads>(k_pcg<float, AM_TCS, MSTRESS_BF16X3, 0, ai::kTcsThreads, 1>, s, a, a.shs.smem, need, tm);
         }
     }
     if (tc) {

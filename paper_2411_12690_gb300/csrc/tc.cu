@@ -75,7 +75,7 @@ bool tc_streamed(int m) {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr int kTcsThreads = 512;
+using ai::kTcsThreads;
 
 // Operator image: B[n][k] = K_r[n][k] (zero padded), rounded to the mode's
 // format; BF16X3 takes the lo part from the FP64 value. Columns are stored in
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kTcThreads) k_apply_tc(const __grid_constant__
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ long long base[kTileTC];
-    __shared__ int offs[3 * kMaxSurf];
+    __shared__ __align__(16) int offs[3 * kMaxSurf];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x;
@@ -140,34 +140,27 @@ __global__ void __launch_bounds__(kTcThreads) k_apply_tc(const __grid_constant__
     if ((tid >> 5) == 0) tc::tmem_free(ts.tmem, (uint32_t)sh.tmem_cols);
 }
 
-// Streamed-operator variant (large bases), 512 threads per CTA.
+// Streamed-operator variant (large bases): warp-specialised CTAs of
+// kTcsThreads threads (apply_items.cuh).
 template <int MODE>
-__global__ void __launch_bounds__(kTcsThreads) k_apply_tcs(const __grid_constant__ ApplyArgs a,
-                                                           const ai::TcsShape sh) {
+__global__ void __launch_bounds__(kTcsThreads, 1) k_apply_tcs(const __grid_constant__ ApplyArgs a,
+                                                              const ai::TcsShape sh) {
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ long long base[kTileTC];
-    __shared__ int offs[3 * kMaxSurf];
-    __shared__ __align__(8) uint64_t bars[8];
+    __shared__ __align__(16) int offs[3 * kMaxSurf];
+    __shared__ __align__(8) uint64_t bars[3 * 4 + 2];
     __shared__ uint32_t tmem_base;
+    __shared__ int fail;
     const int tid = threadIdx.x;
     ai::TcsState ts;
-    ai::tcs_init(ts, sh, smem, bars);
+    ai::tcs_init(ts, sh, smem, bars, &fail);
     if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)sh.tmem_cols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     ts.tmem = tmem_base;
-    bool failed = false;
-    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
-        const ApplyWork it = a.work[w];
-        if (a.st && !a.st[it.array].active) continue;
-        if (!ai::apply_tcs_item<MODE>(a, sh, it, ts, base, offs)) {
-            failed = true;
-            break;
-        }
-    }
-    if (failed) {
+    if (!ai::tcs_apply_phase<MODE>(a, sh, ts, base, offs, blockIdx.x, gridDim.x)) {
         if (tid == 0) atomicExch(a.err, 1);
         ai::tcs_drain(ts, sh);
     }
@@ -182,7 +175,7 @@ bool tc_supported(int m) {
     if (!tc_streamed(m)) return true;
     for (int prec : {MSTRESS_TF32, MSTRESS_BF16, MSTRESS_BF16X3}) {
         ai::TcsShape s = tcs_shape(m, prec);
-        if (s.npad > 512 || s.stages < 2) return false;
+        if (s.npad > 512 || s.stages < 2 || s.stages > 4) return false;
     }
     return true;
 }
