@@ -15,17 +15,40 @@ void mstress_ctx_s::budget_check(size_t bytes) const {
                                         std::to_string(opts.hbm_budget) + " B"};
 }
 
+namespace {
+constexpr size_t kAllocGrain = 512;
+constexpr size_t kCacheCap = size_t(8) << 30;   // freed bytes kept for reuse at most
+}  // namespace
+
 void* mstress_ctx_s::alloc(size_t bytes) {
-    if (bytes == 0) bytes = 16;
+    bytes = round_up(bytes == 0 ? 16 : bytes, kAllocGrain);
     budget_check(bytes);
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Error{MSTRESS_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)};
+    size_t got = bytes;
+    auto it = cache.lower_bound(bytes);
+    if (it != cache.end() && it->first <= 2 * bytes) {
+        // a block freed earlier on this context's stream: wait (normally a
+        // no-op) until the work that used it is done, then reuse it
+        if (cudaEventQuery(it->second.ev) != cudaSuccess) cudaEventSynchronize(it->second.ev);
+        cudaEventDestroy(it->second.ev);
+        p = it->second.p;
+        got = it->first;
+        cached -= got;
+        cache.erase(it);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            trim(0);
+            e = cudaMalloc(&p, bytes);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{MSTRESS_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)};
+        }
     }
-    allocs[p] = bytes;
-    in_use += bytes;
+    allocs[p] = got;
+    in_use += got;
     if (in_use > peak) peak = in_use;
     return p;
 }
@@ -33,9 +56,31 @@ void* mstress_ctx_s::alloc(size_t bytes) {
 void mstress_ctx_s::release(void* p) {
     auto it = allocs.find(p);
     if (it == allocs.end()) return;
-    in_use -= it->second;
+    const size_t bytes = it->second;
+    in_use -= bytes;
     allocs.erase(it);
-    cudaFree(p);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (ev) cudaEventDestroy(ev);
+        cudaFree(p);
+        return;
+    }
+    cache.insert({bytes, Cached{p, ev}});
+    cached += bytes;
+    if (cached > kCacheCap) trim(kCacheCap / 2);
+}
+
+void mstress_ctx_s::trim(size_t keep) {
+    while (cached > keep && !cache.empty()) {
+        auto it = std::prev(cache.end());   // largest first
+        cudaEventSynchronize(it->second.ev);
+        cudaEventDestroy(it->second.ev);
+        cudaFree(it->second.p);
+        cached -= it->first;
+        cache.erase(it);
+    }
 }
 
 namespace ms {
@@ -181,6 +226,7 @@ void mstress_free_ctx(mstress_ctx ctx) {
     if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->allocs) cudaFree(kv.first);
     ctx->allocs.clear();
+    ctx->trim(0);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
     delete ctx;
 }

@@ -120,6 +120,16 @@ struct mstress_ctx_s {
     mstress_opts opts{};
     size_t in_use = 0, peak = 0;
     std::map<void*, size_t> allocs;
+    // Freed blocks kept for reuse (size -> block, event recorded on the
+    // context stream at release): repeated solves of the same shapes allocate
+    // without cudaMalloc / cudaFree (which would synchronise the device).
+    struct Cached {
+        void* p;
+        cudaEvent_t ev;
+    };
+    std::multimap<size_t, Cached> cache;
+    size_t cached = 0;
+    void trim(size_t keep);   // free cached blocks until at most keep bytes remain
     std::string last_error;
     // pinned host words for polling device flags
     int* h_flag = nullptr;

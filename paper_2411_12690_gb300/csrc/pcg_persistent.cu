@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         ts.sA = smem + NS * a.sh.b_plane;
         for (uint32_t i = tid; i < NS * a.sh.a_plane / 16; i += NT)
             reinterpret_cast<uint4*>(ts.sA)[i] = make_uint4(0, 0, 0, 0);
-        if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.sh.tmem_cols);
+        if ((tid >> 5) == 0) tc::tmem_alloc_c<128>(&tmem_base);   // npad <= 128 on this path
         if (tid == 0) tc::mbar_init(&mbar, 1);
         tc::fence_before();
         __syncthreads();
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         if (*(volatile int*)a.abort) tc::mbar_wait(&mbar, ts.phase ^ 1u, 1 << 20);   // bounded drain
         tc::fence_before();
         __syncthreads();
-        if ((tid >> 5) == 0) tc::tmem_free(ts.tmem, (uint32_t)a.sh.tmem_cols);
+        if ((tid >> 5) == 0) tc::tmem_free_c<128>(ts.tmem);
     }
     if constexpr (AM == AM_TCS) {
         if (*(volatile int*)a.abort) ai::tcs_drain(tss, a.shs);
@@ -344,8 +344,8 @@ bool launch_coop(KER kernel, mstress_sol_s* s, PcgArgs& a, size_t smem, int need
     if (e != cudaSuccess || per_sm < 1) { cudaGetLastError(); return false; }
     if (tmem_cols > 0) per_sm = std::min(per_sm, 512 / tmem_cols);
     per_sm = std::min(per_sm, 4);   // more CTAs only lengthen the barriers
-    const int grid = std::max(1, std::min(needed, per_sm * s->ctx->num_sms));
     void* args[] = {&a};
+    const int grid = std::max(1, std::min(needed, per_sm * s->ctx->num_sms));
     e = cudaLaunchCooperativeKernel((void*)kernel, grid, NT, args, smem, s->ctx->stream);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     note_launches(1);
@@ -423,19 +423,17 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     if (tc) {
         a.sh = tc_shape(m, prec);
         a.sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
+        if (a.sh.tmem_cols > 128) return false;   // the kernel allocates 128 tensor-memory columns
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
         const int need = std::max(a.apply_items, vneed);
         switch (prec) {
             case MSTRESS_TF32:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1>, s, a, a.sh.smem, need,
-                                        a.sh.tmem_cols);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1>, s, a, a.sh.smem, need, 128);
             case MSTRESS_BF16:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 1>, s, a, a.sh.smem, need,
-                                        a.sh.tmem_cols);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 1>, s, a, a.sh.smem, need, 128);
             default:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 1>, s, a, a.sh.smem, need,
-                                        a.sh.tmem_cols);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 1>, s, a, a.sh.smem, need, 128);
         }
     }
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
