@@ -729,8 +729,8 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     }
     // tensor-core apply tiles: the largest of 128 / 64 / 32 blocks that still
     // gives every SM two tiles (the tile's gather, not its MMA, sets the time)
-    s->tc_tile = kTileTC;
-    while (s->tc_tile > 32 && total_blocks < (int64_t)s->tc_tile * 2 * ctx->num_sms) s->tc_tile /= 2;
+    s->tc_tile = (int)std::min<int64_t>(kTileTC, std::max<int64_t>(8, round_up((total_blocks + ctx->num_sms - 1) /
+                                                                                   ctx->num_sms, 8)));
     int64_t vec_off = 0, block_off = 0;
     for (int a = 0; a < s->n_arrays; ++a) {
         const mstress_layout* L = in[a].L;

@@ -48,6 +48,54 @@ __device__ __forceinline__ double cta_fold8(const double* v, int n, double* sh8)
     return t;
 }
 
+// Two fixed-order sums at once (the <r,z> and <r,r> partials of one array):
+// the same slices and order as cta_fold8 for each, with the loads of both in
+// flight together. Results valid in thread 0. Needs all threads.
+__device__ __forceinline__ void cta_fold8_2(const double* v1, const double* v2, int n, double* sh16, double& t1,
+                                            double& t2) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < 8) {
+        const int b = (int)((long long)n * w / 8), e = (int)((long long)n * (w + 1) / 8);
+        double s1 = 0, s2 = 0;
+        int i = b + lane;
+        for (; i + 96 < e; i += 128) {
+            const double a0 = __ldcg(v1 + i), a1 = __ldcg(v1 + i + 32), a2 = __ldcg(v1 + i + 64),
+                         a3 = __ldcg(v1 + i + 96);
+            const double c0 = __ldcg(v2 + i), c1 = __ldcg(v2 + i + 32), c2 = __ldcg(v2 + i + 64),
+                         c3 = __ldcg(v2 + i + 96);
+            s1 += a0;
+            s1 += a1;
+            s1 += a2;
+            s1 += a3;
+            s2 += c0;
+            s2 += c1;
+            s2 += c2;
+            s2 += c3;
+        }
+        for (; i < e; i += 32) {
+            s1 += __ldcg(v1 + i);
+            s2 += __ldcg(v2 + i);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            sh16[w] = s1;
+            sh16[8 + w] = s2;
+        }
+    }
+    __syncthreads();
+    t1 = 0;
+    t2 = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) {
+            t1 += sh16[k];
+            t2 += sh16[8 + k];
+        }
+    __syncthreads();
+}
+
 // Block sum of FP32 per-thread values in a fixed order: FP32 butterfly within
 // each warp, the warp sums added in FP64 by thread 0 (the FP64 pipe of the
 // GPU is narrow, so only blockDim.x / 32 FP64 additions). Result valid in

@@ -12,10 +12,10 @@
 // The folds are ordered by work-item index only, so an array's arithmetic is
 // the same alone and inside any batch. A CTA reports its finished work items
 // of an array with one atomic per array per phase (not one per item), and
-// reads an array's scalars once per phase. The grid barrier is two-level (8
-// arrival counters on separate cache lines, then a root) and, like the
-// tensor-core completion wait, spins with an iteration limit; on expiry the
-// kernel records an error, releases its tensor memory and returns.
+// reads an array's scalars once per phase. The grid barrier is one growing
+// arrival counter and, like the tensor-core completion waits, spins with an
+// iteration limit; on expiry the kernel records an error, releases its tensor
+// memory and returns.
 #include <algorithm>
 
 #include "apply_items.cuh"
@@ -25,9 +25,6 @@ namespace ms {
 namespace {
 
 enum { AM_FP64 = 0, AM_TC = 1, AM_SIMT32 = 2, AM_TCS = 3 };
-constexpr int kBarLine = 32;   // unsigned words per barrier cache line
-// barrier words: sub-counters at kBarLine * g (g < 8), root at 8 kBarLine, generation at 9 kBarLine
-constexpr int kBarRoot = 8 * kBarLine, kBarGen = 9 * kBarLine;
 
 struct PcgArgs {
     ApplyArgs ap;              // x = p, z = z, st, Y
@@ -44,7 +41,7 @@ struct PcgArgs {
     PcgState* st;
     double *part_pq, *part_rz, *part_rr;
     int* tickets;              // 2 per array: phase B, phase C
-    unsigned* bar;             // barrier words (see kBarRoot, kBarGen)
+    unsigned* bar;             // grid-barrier arrival counter (zero at launch)
     int* n_active;             // arrays still iterating
     int* err;                  // 1: tensor-core wait expired, 2: grid barrier expired
     int* abort;
@@ -68,44 +65,32 @@ __device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned
     }
 }
 
-// Two-level grid barrier with a bounded wait. CTA b arrives on sub-counter
-// b % 8; the last arrival of each group arrives on the root; the last root
-// arrival resets the counters and advances the generation that everyone
-// waits on. Returns false (in every thread of the CTA) when the grid is
-// aborting or the wait expired.
-__device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok) {
+// Grid barrier with a bounded wait, on one counter that only grows: in the
+// k-th barrier of a launch every CTA adds 1 and waits until the counter
+// reaches (k+1) * gridDim.x (compared as a signed difference, so the counter
+// may wrap). The last arrival needs one atomic round trip, the others see it
+// on their next poll. *k_bar is the CTA's barrier count (shared). Returns
+// false (in every thread of the CTA) when the grid is aborting or the wait
+// expired.
+__device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok, unsigned* k_bar) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* gen = a.bar + kBarGen;
-        const unsigned g = *gen;            // read before arriving: cannot advance without us
-        const unsigned G = gridDim.x, grp = blockIdx.x & 7u;
-        const unsigned groups = G < 8u ? G : 8u;
-        const unsigned gsize = (G - grp + 7u) / 8u;   // CTAs b < G with b % 8 == grp
+        const unsigned target = (*k_bar + 1u) * gridDim.x;
+        *k_bar += 1u;
+        volatile unsigned* ctr = a.bar;
         __threadfence();
-        bool last = false;
-        if (atomicAdd(a.bar + kBarLine * grp, 1u) == gsize - 1u) {
-            atomicExch(a.bar + kBarLine * grp, 0u);
-            __threadfence();
-            if (atomicAdd(a.bar + kBarRoot, 1u) == groups - 1u) {
-                atomicExch(a.bar + kBarRoot, 0u);
-                last = true;
-            }
-        }
-        if (last) {
-            __threadfence();
-            atomicAdd(a.bar + kBarGen, 1u);
-        } else {
+        if ((int)(atomicAdd(a.bar, 1u) + 1u - target) < 0) {
             long long spins = 0;
-            while (*gen == g) {
-                if (*(volatile int*)a.abort) { ok = 0; break; }
+            while ((int)(*ctr - target) < 0) {
+                if ((spins & 63) == 63 && *(volatile int*)a.abort) { ok = 0; break; }
                 if (++spins > (1LL << 25)) {
                     atomicExch(a.err, 2);
                     atomicExch(a.abort, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(20);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -127,8 +112,9 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ long long base[kTileTC];
     __shared__ __align__(16) int offs[3 * kMaxSurf];
-    __shared__ double shr[NT / 32], sh8[8];
+    __shared__ double shr[NT / 32], sh8[16];
     __shared__ int s_flag, s_ok, s_active;
+    __shared__ unsigned s_kbar;   // grid barriers passed by this CTA
     __shared__ double s_scalar;
     __shared__ ArrayDev s_A;
     __shared__ __align__(8) uint64_t mbar;
@@ -197,8 +183,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                         }
                     }
                 } else {
-                    const double rz = pi::cta_fold8(a.part_rz + s_A.vwork_off, s_A.n_vwork, sh8);
-                    const double rr = pi::cta_fold8(a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8);
+                    double rz, rr;
+                    pi::cta_fold8_2(a.part_rz + s_A.vwork_off, a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8, rz, rr);
                     if (tid == 0) {
                         a.tickets[2 * kk + 1] = 0;
                         PcgState s;
@@ -240,6 +226,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         }
     };
 
+    if (tid == 0) s_kbar = 0;   // read first by thread 0 itself in the first barrier
     unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
@@ -273,7 +260,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             atomicExch(a.err, 1);
             atomicExch(a.abort, 1);
         }
-        if (!grid_sync(a, &s_ok)) break;
+        if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 0, t_prev);
         // ---- phase B: interface sum, <p, q>, alpha
         {
@@ -292,7 +279,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             }
             switch_array(cur, -1, 1);
         }
-        if (!grid_sync(a, &s_ok)) break;
+        if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 1, t_prev);
         // ---- phase C: vector update, <r,z>, <r,r>, beta, stopping test
         {
@@ -315,7 +302,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             }
             switch_array(cur, -1, 2);
         }
-        if (!grid_sync(a, &s_ok)) break;
+        if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 2, t_prev);
         if (a.timers && blockIdx.x == 0 && tid == 0) a.timers[3] += 1;
         if (*(volatile int*)a.n_active <= 0) break;
@@ -406,7 +393,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     }
     if (tc && tc_streamed(m)) {
         a.shs = tcs_shape(m, prec);
-        a.shs.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
+        a.shs.lg_tile = lg_ceil(s->tc_tile);
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
         const int need = std::max(a.apply_items, vneed);
@@ -422,7 +409,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     }
     if (tc) {
         a.sh = tc_shape(m, prec);
-        a.sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
+        a.sh.lg_tile = lg_ceil(s->tc_tile);
         if (a.sh.tmem_cols > 128) return false;   // the kernel allocates 128 tensor-memory columns
         a.apply_items = s->n_awork_tc;
         a.panels = 1;

@@ -50,6 +50,9 @@ __device__ __forceinline__ V p_next(V z, V p, V beta) {
     return fma(beta, p, z);
 }
 
+// log2 of the smallest power of two >= v (v >= 1): rows spanned by a tile.
+inline int lg_ceil(int v) { return v <= 1 ? 0 : 32 - __builtin_clz((unsigned)(v - 1)); }
+
 // Per-tile gather set-up: lattice base index of each block of the tile and
 // the per-array offset of each element DOF (Lagrange node (a, b, c) of the
 // block sits on lattice point (i(n-1)+a, j(n-1)+b, c)).
@@ -83,7 +86,8 @@ struct mstress_sol_s {
     ms::DBuf d_lm, d_arrays, d_bref, d_blist, d_awork, d_awork_tc, d_awork_rec, d_vwork, d_site;
     int n_awork = 0, n_awork_tc = 0, n_awork_rec = 0, n_vwork = 0;
     std::vector<ms::ApplyWork> h_awork, h_awork_rec;   // host copies (filtered recovery)
-    int tc_tile = 128;                    // blocks per tensor-core apply tile (<= 128; smaller tiles
+    int tc_tile = 128;                    // blocks per tensor-core apply tile (<= 128, a multiple of 8: about
+                                          // one tile per SM when the batch is small; smaller tiles
                                           // spread a small array's gather over more SMs)
     ms::DBuf b, dinv, fixed;              // FP64 right-hand side, Jacobi inverse (0 on constrained DOFs)
     ms::DBuf dinv32;                      // Jacobi inverse in FP32 (inner PCG of the mixed modes)

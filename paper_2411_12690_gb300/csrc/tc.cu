@@ -214,7 +214,7 @@ void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a) {
     cudaStream_t st = s->ctx->stream;
     if (tc_streamed(s->m)) {
         ai::TcsShape sh = tcs_shape(s->m, prec);
-        sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
+        sh.lg_tile = lg_ceil(s->tc_tile);
         MS_REQUIRE(sh.npad <= 512 && sh.stages >= 2, MSTRESS_EINVAL, "basis too large for the tensor-core tile");
         const int per_sm = sh.tmem_cols <= 256 ? 2 : 1;
         const int grid = std::max(1, std::min(a.n_work, s->ctx->num_sms * per_sm));
@@ -227,7 +227,7 @@ void launch_apply_tc(mstress_sol_s* s, int prec, const ApplyArgs& a) {
         return;
     }
     ai::TcShape sh = tc_shape(s->m, prec);
-    sh.lg_tile = __builtin_ctz((unsigned)s->tc_tile);
+    sh.lg_tile = lg_ceil(s->tc_tile);
     MS_REQUIRE(sh.npad <= 256 && sh.smem <= 200 * 1024, MSTRESS_EINVAL, "basis too large for the tensor-core tile");
     const int per_sm = sh.smem > 100 * 1024 ? 1 : 2;   // TMEM: <= 2 x 256 columns per SM
     const int grid = std::max(1, std::min(a.n_work, s->ctx->num_sms * per_sm));
