@@ -33,6 +33,10 @@ METRIC = "TSV blocks solved+recovered/s (100x100 array)"
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
 DTYPE = {"fp64": "f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64", "bf16x3": "bf16x3+f32+f64"}
 ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch divided by
+# the launch's PCG iterations, per precision (profiles/k_pcg_array100.md);
+# absent until taken for the current kernel.
+PCG_TRAFFIC = {"bf16x3": 99200}   # 7.60 MB read + 0.73 MB written over the launch's ~84 iterations
 
 
 def parse():
@@ -258,49 +262,76 @@ def ours(args):
     e2e_value = world * n_blocks * args.steps / float(et.item())
 
     # roofline of the dominant kernel. The PCG runs as one persistent kernel
-    # whose phases are timed on the device (globaltimer at its grid barriers);
-    # the recovery kernel is timed with CUDA events on the context stream.
+    # (k_pcg) whose phases are timed on the device (globaltimer at its grid
+    # barriers); the recovery kernel is timed with CUDA events on the context
+    # stream. Algorithmic work per PCG iteration (N blocks, m = 78, n_vec
+    # lattice DOFs, w vector bytes, w_in operand bytes per coefficient):
+    #   a3 apply   bytes = C read m N w_in + Y write m N w + vectors 2 n_vec w,
+    #              flops = 2 m^2 N per operand product (3 products in bf16x3)
+    #   a4 vectors bytes = 10 vector passes of n_vec w
+    #   a6 recovery flops = 2 (6 N_el) (m+1) N (Gauss-mean stress modes: 8x
+    #              fewer than the 48 N_el Gauss-point rows), VM out N_el N 4 B
     sol = step(vm_dev)
     info = sol.info()
     ph = sol.phase_ms()
     t_rec = api.profile(ctx, sol, 3, 5)
     n_iter = max(1, ph["iterations"])
     m = 78
-    lat_dofs = 3 * (2 * nx + 1) * (2 * ny + 1) * 3          # lattice DOFs of the 100x100 array (n = 3)
-    apply_flops = 2.0 * m * m * n_blocks * (3 if prec == 3 else 1)
-    rec_flops = 2.0 * 6 * n_el * (m + 1) * n_blocks * (3 if prec == 3 else 1)
+    n_vec = 3 * (2 * nx + 1) * (2 * ny + 1) * 3          # lattice DOFs of the array (n = 3)
     w = 8 if prec == 0 else 4
-    # algorithmic bytes of one PCG iteration: gather p, z per element DOF and
-    # write Y; read Y, p, z, D^-1 and write p, q; read p, q, x, r, D^-1 and write x, r, z
-    it_bytes = (2 * w * m * n_blocks + w * 80 * n_blocks) + (w * m * n_blocks + lat_dofs * (2 * w + 8 + 2 * w)) \
-        + lat_dofs * (4 * w + 8 + 3 * w)
+    w_in = {0: 8, 1: 4, 2: 2, 3: 4}[prec]
+    products = 3 if prec == 3 else 1
+    a3_bytes = m * n_blocks * w_in + m * n_blocks * w + 2 * n_vec * w
+    a4_bytes = 10 * n_vec * w
+    it_bytes = a3_bytes + a4_bytes
+    a3_flops = 2.0 * m * m * n_blocks * products
+    rec_flops = 2.0 * 6 * n_el * (m + 1) * n_blocks * products
+    rec_bytes = n_el * n_blocks * (8 if prec == 0 else 4)
     sm_mhz = clk.get("sm_mhz") or 1900.0
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    hbm = peaks.get("hbm_gbs")
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks.get("hbm_gbs") else "fallback 6800 GB/s"
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    # tensor peak of the mode's operand type: bf16 measured; tf32 = bf16 x nominal 1.1 / 2.25
+    tensor_peak = {1: bf16 * 1.1 / 2.25, 2: bf16, 3: bf16}.get(prec)
+    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12     # 152 SMs x 2 DFMA/clk at the sampled SM clock
+    t_apply = ph["apply"] / n_iter
     t_pcg = (ph["apply"] + ph["isum"] + ph["update"]) / n_iter        # ms per iteration
     share = {"pcg": ph["apply"] + ph["isum"] + ph["update"], "recover": t_rec}
     if prec == 0:
-        # FP64 pipe: 152 SMs x 2 DFMA/clk (4 flop/clk) at the sampled SM clock
-        fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": apply_flops / (ph["apply"] / n_iter * 1e-3) / 1e12, "peak": fp64_peak,
+        roof = {"bound": "alu", "achieved": a3_flops / (t_apply * 1e-3) / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "traffic": None,
                 "kernel": "k_pcg<FP64> phase A (element products on the FP64 pipe)",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock (probe measured 1.257 TFLOP/s)"}
     else:
+        tr = PCG_TRAFFIC.get(args.precision)
         roof = {"bound": "hbm", "achieved": it_bytes / (t_pcg * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "traffic": None, "kernel": "k_pcg<tensor-core> (persistent PCG iteration: apply + interface sum + update)",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800 GB/s"}
-        if not hbm:
-            roof["peak"] = 6800.0
+                "traffic": tr,
+                "kernel": "k_pcg (persistent PCG: tensor-core apply + interface sum + vector update)",
+                "peak_source": hbm_src,
+                "note": "vectors are L2-resident at this size, so the iteration is latency-bound (three grid "
+                        "barriers and folds per iteration), not HBM-bound; traffic = ncu dram bytes of one "
+                        "k_pcg launch divided by its iterations (profiles/)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["per_iteration_ms"] = {"apply": ph["apply"] / n_iter, "isum": ph["isum"] / n_iter,
-                                "update": ph["update"] / n_iter}
+    roof["algorithmic_bytes_per_iteration"] = it_bytes
+    roof["per_iteration_ms"] = {"apply": t_apply, "isum": ph["isum"] / n_iter, "update": ph["update"] / n_iter}
+    roof["a3_apply"] = {"bytes": a3_bytes, "flops": a3_flops, "ms": t_apply,
+                        "gbs": a3_bytes / (t_apply * 1e-3) / 1e9, "frac_hbm": a3_bytes / (t_apply * 1e-3) / 1e9 / hbm,
+                        "tflops": a3_flops / (t_apply * 1e-3) / 1e12}
+    roof["a6_recover"] = {"flops": rec_flops, "ms": t_rec, "tflops": rec_flops / (t_rec * 1e-3) / 1e12,
+                          "out_bytes": rec_bytes, "gbs": rec_bytes / (t_rec * 1e-3) / 1e9,
+                          "frac_hbm": rec_bytes / (t_rec * 1e-3) / 1e9 / hbm}
+    if tensor_peak:
+        roof["a3_apply"]["frac_tensor"] = roof["a3_apply"]["tflops"] / tensor_peak
+        roof["a6_recover"]["frac_tensor"] = roof["a6_recover"]["tflops"] / tensor_peak
+        roof["a6_recover"]["tensor_peak_tflops"] = tensor_peak
+    else:
+        roof["a6_recover"]["frac_fp64"] = roof["a6_recover"]["tflops"] / fp64_peak
     roof["recover_ms"] = t_rec
-    roof["recover_tflops"] = rec_flops / (t_rec * 1e-3) / 1e12
     roof["time_share"] = {k: v / sum(share.values()) for k, v in share.items()}
     sol.close()
 
@@ -378,7 +409,35 @@ def batch_bench(args):
                           "max_rel_res": max(i["rel_res"] for i in infos),
                           "solve_ms": 1e3 * sum(a for a, _ in split) / len(split),
                           "recover_ms": 1e3 * sum(b for _, b in split) / len(split),
-                          "persistent_phase_ms": phases}}), flush=True)
+                          "persistent_phase_ms": phases},
+                      "roofline": batch_roofline(args, jobs, n_blocks, n_el, phases,
+                                                 1e3 * sum(b for _, b in split) / len(split))}), flush=True)
+
+
+def batch_roofline(args, jobs, n_blocks, n_el, ph, rec_ms):
+    """a3 (element products, per PCG iteration) and a6 (recovery) of the batch
+    against the measured HBM peak: a3 bytes = C read m N w_in + Y write m N 4 +
+    vectors 2 n_vec 4; a6 bytes = the per-element von Mises written (N n_el 4)."""
+    m, prec = 294, PREC[args.precision]
+    n_vec = sum(3 * (j.site_type.shape[1] * 4 + 1) * (j.site_type.shape[0] * 4 + 1) * 5 for j in jobs)
+    w = 8 if prec == 0 else 4
+    w_in = {0: 8, 1: 4, 2: 2, 3: 4}[prec]
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs") or 6800.0
+    except OSError:
+        hbm = 6800.0
+    it = max(1, ph["iterations"])
+    t_apply = ph["apply"] / it
+    a3_bytes = m * n_blocks * w_in + m * n_blocks * w + 2 * n_vec * w
+    rec_bytes = n_blocks * n_el * w
+    a3 = {"bytes": a3_bytes, "ms": t_apply, "gbs": a3_bytes / (t_apply * 1e-3) / 1e9}
+    a3["frac"] = a3["gbs"] / hbm
+    a6 = {"bytes": rec_bytes, "ms": rec_ms, "gbs": rec_bytes / (rec_ms * 1e-3) / 1e9}
+    a6["frac"] = a6["gbs"] / hbm
+    return {"bound": "hbm", "achieved": a3["gbs"], "peak": hbm, "unit": "GB/s", "frac": a3["frac"],
+            "traffic": None, "kernel": "k_pcg phase A (streamed tensor-core element products, per iteration)",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "a3_apply": a3, "a6_recover": a6,
+            "lattice_dofs": n_vec}
 
 
 def serve_bench(args):

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_isum(const __grid_constant__ IsumA
         if (a.st && !a.st[it.array].active) continue;
         const ArrayDev A = a.arrays[it.array];
         const V beta = a.st ? (V)a.st[it.array].beta : V(0);
-        const V acc = pi::isum_item<4, V, YT>(it, A, a.lm, static_cast<const V*>(a.dinv), a.ldY,
+        const pi::DotAcc<V> acc = pi::isum_item<4, V, YT>(it, A, a.lm, static_cast<const V*>(a.dinv), a.ldY,
                                               static_cast<const YT*>(a.Y), static_cast<V*>(a.p),
                                               static_cast<const V*>(a.z), static_cast<V*>(a.q), beta);
         if (a.part_pq) {
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_vec1(const __grid_constant__ VecAr
         }
         __syncthreads();
         const V al = (V)s_alpha;
-        V srz, srr;
+        pi::DotAcc<V> srz, srr;
         pi::vec1_item<4, V>(it, static_cast<const V*>(a.dinv_v), al, x, r, z, p, q, srz, srr);
         const double rz = block_sum(srz, sh);
         const double rr = block_sum(srr, sh);

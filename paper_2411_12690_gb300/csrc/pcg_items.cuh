@@ -96,21 +96,64 @@ __device__ __forceinline__ void cta_fold8_2(const double* v1, const double* v2, 
     __syncthreads();
 }
 
-// Block sum of FP32 per-thread values in a fixed order: FP32 butterfly within
-// each warp, the warp sums added in FP64 by thread 0 (the FP64 pipe of the
-// GPU is narrow, so only blockDim.x / 32 FP64 additions). Result valid in
-// thread 0.
-__device__ __forceinline__ double block_sum(float v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Dot-product accumulators. FP64 vectors: a double. FP32 vectors: a
+// double-FP32 pair (hi + lo) built from error-free transformations on the
+// FP32 pipe (the exact product by fma, the exact sum by TwoSum), about 48
+// significant bits, so the inner PCG's dot products keep FP64-level accuracy
+// without the GPU's narrow FP64 pipe; the pairs are folded in FP64 across
+// warps and work items.
+template <class V>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+};
+
+template <>
+struct DotAcc<float> {
+    float hi = 0, lo = 0;
+    // (the _rn intrinsics are never contracted into fused operations)
+    __device__ __forceinline__ static void two_sum(float a, float b, float& sum, float& err) {
+        sum = __fadd_rn(a, b);
+        const float bb = __fsub_rn(sum, a);
+        err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+    }
+    __device__ __forceinline__ void add(float x, float y) {
+        const float p = __fmul_rn(x, y), pe = fmaf(x, y, -p);   // x y = p + pe exactly
+        float sum, err;
+        two_sum(hi, p, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, __fadd_rn(err, pe));
+    }
+    __device__ __forceinline__ void merge(float ohi, float olo) {
+        float sum, err;
+        two_sum(hi, ohi, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, __fadd_rn(err, olo));
+    }
+};
+
+// Block sum of double-FP32 accumulators in a fixed order: butterfly of the
+// pairs within each warp, the warp sums (hi + lo in FP64) added in FP64 by
+// thread 0. Result valid in thread 0.
+__device__ __forceinline__ double block_sum(DotAcc<float> v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, v.hi, o), olo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v.merge(ohi, olo);
+    }
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[w] = (double)v;
+    if ((threadIdx.x & 31) == 0) sh[w] = (double)v.hi + (double)v.lo;
     __syncthreads();
     double t = 0;
     if (threadIdx.x == 0)
         for (int k = 0; k < nw; ++k) t += sh[k];
     return t;
 }
+
+__device__ __forceinline__ double block_sum(DotAcc<double> v, double* sh);
 
 // Block sum (blockDim.x threads, multiple of 32) in a fixed order; result valid in all threads.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -123,6 +166,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int k = 0; k < nw; ++k) t += sh[k];
     return t;
 }
+
+__device__ __forceinline__ double block_sum(DotAcc<double> v, double* sh) { return block_sum(v.s, sh); }
 
 __device__ __forceinline__ void lattice_coords(const ArrayDev& A, long long g, int& comp, int& gx, int& gy, int& gz) {
     // an array's lattice holds fewer than 2^31 DOFs, so 32-bit division suffices
@@ -167,13 +212,13 @@ __device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __r
 // dependent ones. The owner candidates are visited rows ascending then columns
 // ascending, as in for_owners; constrained rows are zeroed after the sum.
 template <int U, class V, class YT>
-__device__ __forceinline__ V isum_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm, const V* dinv, int ldY,
+__device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm, const V* dinv, int ldY,
                                        const YT* __restrict__ Y, V* __restrict__ p, const V* __restrict__ z,
                                        V* __restrict__ q, V beta) {
     const int n = lm->n, n1 = n - 1;
     const int16_t* __restrict__ surf = lm->surf_idx;
     const long long end = it.start + it.count;
-    V acc = 0;
+    DotAcc<V> acc;
     for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
         V s[U], dv[U];
         V pv[U], zv[U];
@@ -216,7 +261,7 @@ __device__ __forceinline__ V isum_item(const VecWork& it, const ArrayDev& A, con
                     p[g] = pn;
                 }
                 q[g] = sv;
-                acc = fma(pn, sv, acc);
+                acc.add(pn, sv);
             }
         }
     }
@@ -228,9 +273,9 @@ __device__ __forceinline__ V isum_item(const VecWork& it, const ArrayDev& A, con
 // (U DOFs per thread in flight).
 template <int U, class V>
 __device__ __forceinline__ void vec1_item(const VecWork& it, const V* dinv, V al, V* x, V* r, V* z, const V* p,
-                                          const V* q, V& srz, V& srr) {
-    srz = 0;
-    srr = 0;
+                                          const V* q, DotAcc<V>& srz, DotAcc<V>& srr) {
+    srz = DotAcc<V>();
+    srr = DotAcc<V>();
     const long long end = it.start + it.count;
     for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
         V pv[U], qv[U], xv[U], rv0[U], dv[U];
@@ -254,8 +299,8 @@ __device__ __forceinline__ void vec1_item(const VecWork& it, const V* dinv, V al
                 const V zv = dv[u] * rv;
                 r[g] = rv;
                 z[g] = zv;
-                srz = fma(rv, zv, srz);
-                srr = fma(rv, rv, srr);
+                srz.add(rv, zv);
+                srr.add(rv, rv);
             }
         }
     }

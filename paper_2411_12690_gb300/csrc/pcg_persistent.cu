@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 if (w + (int)gridDim.x < a.n_vwork) next = a.vwork[w + gridDim.x];   // overlaps this item
                 if (it.array != cur.k) switch_array(cur, it.array, 1);
                 if (!s_active) continue;
-                const V acc = pi::isum_item<sizeof(V) == 8 ? 2 : 4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
+                const pi::DotAcc<V> acc = pi::isum_item<sizeof(V) == 8 ? 2 : 4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
                                                      static_cast<const V*>(a.ap.Y), p, z, q, (V)s_scalar);
                 const double t = pi::block_sum(acc, shr);
                 if (tid == 0) a.part_pq[w] = t;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 if (w + (int)gridDim.x < a.n_vwork) next = a.vwork[w + gridDim.x];
                 if (it.array != cur.k) switch_array(cur, it.array, 2);
                 if (!s_active) continue;
-                V srz, srr;
+                pi::DotAcc<V> srz, srr;
                 pi::vec1_item<NT >= 512 ? 8 : 4, V>(it, static_cast<const V*>(a.dinv), (V)s_scalar, x, r, z, p, q, srz, srr);
                 const double rz = pi::block_sum(srz, shr);
                 const double rr = pi::block_sum(srr, shr);
