@@ -36,7 +36,7 @@ ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch divided by
 # the launch's PCG iterations, per precision (profiles/k_pcg_array100.md);
 # absent until taken for the current kernel.
-PCG_TRAFFIC = {"bf16x3": 99200}   # 7.60 MB read + 0.73 MB written over the launch's ~84 iterations
+PCG_TRAFFIC = {}
 
 
 def parse():

@@ -747,7 +747,9 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         A.block_off = block_off;
         A.dT = in[a].dT;
         A.vwork_off = (int)vwork.size();
-        const int64_t chunk = s->precision == MSTRESS_FP64 ? kVecChunk64 : kVecChunk32;
+        const int64_t chunk = s->precision == MSTRESS_FP64 || !s->use_tc ? kVecChunk64
+                              : tc_streamed(s->m)                   ? kVecChunk32
+                                                                    : kVecChunkTC;
         for (int64_t st = 0; st < A.n_dof; st += chunk)
             vwork.push_back(VecWork{a, 0, vec_off + st, std::min<int64_t>(chunk, A.n_dof - st)});
         A.n_vwork = (int)vwork.size() - A.vwork_off;

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 if (w + (int)gridDim.x < a.n_vwork) next = a.vwork[w + gridDim.x];   // overlaps this item
                 if (it.array != cur.k) switch_array(cur, it.array, 1);
                 if (!s_active) continue;
-                const pi::DotAcc<V> acc = pi::isum_item<sizeof(V) == 8 ? 2 : 4, V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
+                const pi::DotAcc<V> acc = pi::isum_item<sizeof(V) == 8 ? 2 : (AM == AM_TC ? 5 : 4), V, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
                                                      static_cast<const V*>(a.ap.Y), p, z, q, (V)s_scalar);
                 const double t = pi::block_sum(acc, shr);
                 if (tid == 0) a.part_pq[w] = t;

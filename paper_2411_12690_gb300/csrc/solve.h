@@ -6,10 +6,14 @@
 
 namespace ms {
 
-// Lattice DOFs per vector work item: FP64 solves 2048 (256 threads x 2 rounds
-// of 4), reduced-precision solves 4096 (512 threads x 8). The chunking is a
-// function of the array and the precision only, never of the batch.
+// Lattice DOFs per vector work item, matched to the solver CTA that runs the
+// vector phases: 2048 for 256-thread CTAs (FP64: 2 rounds of 4 per thread),
+// 2560 for the resident tensor-core solver (512 threads x 5: one round, and
+// one item per SM at 100x100), 4096 for the streamed tensor-core solver (512
+// threads x 8). The chunking is a function of the array, the precision and
+// the basis size only, never of the batch.
 constexpr int kVecChunk64 = 2048;
+constexpr int kVecChunkTC = 2560;
 constexpr int kVecChunk32 = 4096;
 constexpr int kTile64 = 32;       // blocks per CUDA-core apply / recovery tile
 constexpr int kTileTC = 128;      // blocks per tensor-core apply tile (the MMA M dimension)
