@@ -415,9 +415,10 @@ def batch_bench(args):
 
 
 def batch_roofline(args, jobs, n_blocks, n_el, ph, rec_ms):
-    """a3 (element products, per PCG iteration) and a6 (recovery) of the batch
-    against the measured HBM peak: a3 bytes = C read m N w_in + Y write m N 4 +
-    vectors 2 n_vec 4; a6 bytes = the per-element von Mises written (N n_el 4)."""
+    """a3 (element products, per PCG iteration) against the measured HBM peak
+    (bytes = C read m N w_in + Y write m N 4 + vectors 2 n_vec 4) and a6 (the
+    recovery) against the tensor peak (flops 2 (6 n_el) (m+1) N per operand
+    product) and HBM (the von Mises written, N n_el 4 bytes)."""
     m, prec = 294, PREC[args.precision]
     n_vec = sum(3 * (j.site_type.shape[1] * 4 + 1) * (j.site_type.shape[0] * 4 + 1) * 5 for j in jobs)
     w = 8 if prec == 0 else 4
@@ -433,7 +434,17 @@ def batch_roofline(args, jobs, n_blocks, n_el, ph, rec_ms):
     a3 = {"bytes": a3_bytes, "ms": t_apply, "gbs": a3_bytes / (t_apply * 1e-3) / 1e9}
     a3["frac"] = a3["gbs"] / hbm
     a6 = {"bytes": rec_bytes, "ms": rec_ms, "gbs": rec_bytes / (rec_ms * 1e-3) / 1e9}
-    a6["frac"] = a6["gbs"] / hbm
+    a6["frac_hbm"] = a6["gbs"] / hbm
+    # flops of the Gauss-mean contraction (x3 operand products in bf16x3)
+    a6["flops"] = 2.0 * 6 * n_el * (m + 1) * n_blocks * (3 if prec == 3 else 1)
+    a6["tflops"] = a6["flops"] / (rec_ms * 1e-3) / 1e12
+    try:
+        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops") or 1900.0
+    except OSError:
+        bf16 = 1900.0
+    tensor_peak = {1: bf16 * 1.1 / 2.25, 2: bf16, 3: bf16}.get(prec)
+    if tensor_peak:
+        a6["frac_tensor"] = a6["tflops"] / tensor_peak
     return {"bound": "hbm", "achieved": a3["gbs"], "peak": hbm, "unit": "GB/s", "frac": a3["frac"],
             "traffic": None, "kernel": "k_pcg phase A (streamed tensor-core element products, per iteration)",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "a3_apply": a3, "a6_recover": a6,

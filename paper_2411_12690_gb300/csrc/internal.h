@@ -120,6 +120,9 @@ struct mstress_ctx_s {
     mstress_opts opts{};
     size_t in_use = 0, peak = 0;
     std::map<void*, size_t> allocs;
+    // tensor-core tile size chosen by the autotuner, per (basis size,
+    // precision, batch-size class)
+    std::map<uint64_t, int> tile_choice;
     // Freed blocks kept for reuse (size -> block, event recorded on the
     // context stream at release): repeated solves of the same shapes allocate
     // without cudaMalloc / cudaFree (which would synchronise the device).

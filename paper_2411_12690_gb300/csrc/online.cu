@@ -727,8 +727,8 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         if (li.bc && li.bc->n_prescribed) any_presc = true;
         total_blocks += (int64_t)li.L->nx * li.L->ny;
     }
-    // tensor-core apply tiles: the largest of 128 / 64 / 32 blocks that still
-    // gives every SM two tiles (the tile's gather, not its MMA, sets the time)
+    // tensor-core apply tiles: about one tile per SM (a multiple of 8 blocks,
+    // at most 128); the autotuner may replace it (solve_prepare)
     s->tc_tile = (int)std::min<int64_t>(kTileTC, std::max<int64_t>(8, round_up((total_blocks + ctx->num_sms - 1) /
                                                                                    ctx->num_sms, 8)));
     int64_t vec_off = 0, block_off = 0;
@@ -779,6 +779,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
             tiles(awork, kTile64);
             tiles(awork_tc, (size_t)s->tc_tile);
             tiles(awork_rec, kTileTC);
+            if (!v.empty()) s->h_seg.push_back(ApplyWork{t, a, start, (int)v.size()});
         }
         if (any_presc) {
             fixed.resize(vec_off + A.n_dof, 0);
@@ -873,6 +874,72 @@ void check_device_error(mstress_sol_s* s) {
     MS_REQUIRE(f[2] == 0, MSTRESS_EDEVICE_TIMEOUT, "a tensor-core wait or a grid barrier timed out on the device");
 }
 
+// Rebuild the tensor-core tile list with tiles of `tile` blocks.
+void set_tc_tiles(mstress_sol_s* s, int tile) {
+    std::vector<ApplyWork> w;
+    for (const ApplyWork& g : s->h_seg)
+        for (int st = 0; st < g.count; st += tile)
+            w.push_back(ApplyWork{g.type, g.array, g.start + st, std::min(tile, g.count - st)});
+    if (s->d_awork_tc.bytes < w.size() * sizeof(ApplyWork))
+        alloc_into(s->ctx, s->d_awork_tc, w.size() * sizeof(ApplyWork), false);
+    MS_CUDA(cudaMemcpyAsync(s->d_awork_tc.ptr, w.data(), w.size() * sizeof(ApplyWork), cudaMemcpyHostToDevice,
+                            s->ctx->stream));
+    s->n_awork_tc = (int)w.size();
+    s->tc_tile = tile;
+}
+
+// Autotuner of the tensor-core tile (the MMA M extent actually filled, i.e.
+// blocks per tile): for each candidate it runs a few iterations of the
+// persistent solver on the solve's own right-hand side and reads the time of
+// the element-product phase from the solver's device timers; the fastest is
+// kept, and cached in the context per (basis size, precision, batch-size
+// class) so later solves of that class skip the search. The trial iterations
+// leave nothing behind: every solve restarts its vectors and scalars.
+void autotune_tc_tile(mstress_sol_s* s) {
+    if (!s->use_tc || s->precision == MSTRESS_FP64 || s->h_seg.empty()) return;
+    mstress_ctx ctx = s->ctx;
+    if (s->n_blocks < 2LL * ctx->num_sms) return;   // at most a few blocks per SM: nothing to choose
+    const int cls = 64 - __builtin_clzll((unsigned long long)s->n_blocks);
+    const uint64_t key = ((uint64_t)s->m << 40) | ((uint64_t)s->precision << 32) | (uint64_t)cls;
+    auto hit = ctx->tile_choice.find(key);
+    if (hit != ctx->tile_choice.end()) {
+        if (hit->second != s->tc_tile) set_tc_tiles(s, hit->second);
+        return;
+    }
+    constexpr int kTrialIters = 6;
+    const int h = s->tc_tile;
+    std::vector<int> cand = {h, 32, 64, 128};
+    for (int c : {(int)round_up(h / 2, 8), (int)round_up(h + h / 2, 8)}) cand.push_back(c);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    cudaStream_t st = ctx->stream;
+    int best = h;
+    double best_ns = -1;
+    for (int c : cand) {
+        if (c < 8 || c > kTileTC) continue;
+        set_tc_tiles(s, c);
+        pcg_start<float>(s, s->v32, s->b.as<double>(), 0.0, kTrialIters, nullptr);
+        MS_CUDA(cudaMemsetAsync(s->timers.ptr, 0, s->timers.bytes, st));
+        if (!pcg_run_persistent(s, s->v32, s->precision, kTrialIters, true)) {
+            best_ns = -1;   // no cooperative launch: keep the default tiles
+            best = h;
+            break;
+        }
+        unsigned long long t[4];
+        MS_CUDA(cudaMemcpyAsync(t, s->timers.ptr, sizeof(t), cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaStreamSynchronize(st));
+        const double ns = t[3] ? (double)t[0] / (double)t[3] : 0.0;
+        if (best_ns < 0 || ns < best_ns) {
+            best_ns = ns;
+            best = c;
+        }
+    }
+    check_device_error(s);
+    MS_CUDA(cudaMemsetAsync(s->timers.ptr, 0, s->timers.bytes, st));
+    ctx->tile_choice[key] = best;
+    if (best != s->tc_tile) set_tc_tiles(s, best);
+}
+
 // a2: right-hand side and Jacobi diagonal, the FP64 element buffer of the
 // mixed modes, and the lifting of prescribed values (Eq. 13).
 void solve_prepare(mstress_sol_s* s) {
@@ -908,6 +975,7 @@ void solve_prepare(mstress_sol_s* s) {
                                                                             s->v64.q.as<double>(), s->dinv.as<double>());
         MS_LAUNCH_CHECK();
     }
+    autotune_tc_tile(s);
 }
 
 // Outer (refinement) state from b: x = 0, ||b||, tolerance, step count 0.
