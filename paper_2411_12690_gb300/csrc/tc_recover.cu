@@ -30,7 +30,6 @@
 namespace ms {
 namespace {
 
-constexpr int kRecThreads = 256;
 constexpr int kElemPerTile = 21;   // 21 elements x 6 components = 126 of 128 rows
 constexpr int kMaxStages = 3;
 
@@ -95,30 +94,45 @@ __global__ void k_smean_image(const double* Smean, int ld, int m1, int n_el, Rec
 // then rows, then groups), so the stores are contiguous and the loads run
 // along a block's lattice DOFs.
 template <int MODE>
-__global__ void k_coeff_image(const __grid_constant__ ApplyArgs a, RecShape sh, uint8_t* out) {
+__global__ void k_coeff_image(const __grid_constant__ ApplyArgs a, RecShape sh, int split, uint8_t* out) {
     constexpr int ESZ = MODE == MSTRESS_TF32 ? 4 : 2;
     constexpr int LGKE = MODE == MSTRESS_TF32 ? 2 : 3;
+    constexpr int U = 4;   // loads in flight per thread
     __shared__ long long base[kTileTC];
     __shared__ int offs[3 * kMaxSurf];
     const double* __restrict__ x = static_cast<const double*>(a.x);
     const uint32_t sbo = tc::sbo_bytes(sh.kpad, ESZ);
     const int total = sh.kpad * kTileTC;
-    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
+    // CTA c of a tile's split CTAs takes the index range [c total / split, (c+1) total / split)
+    for (int wc = blockIdx.x; wc < a.n_work * split; wc += gridDim.x) {
+        const int w = wc / split, c = wc - w * split;
         const ApplyWork it = a.work[w];
         const ArrayDev A = a.arrays[it.array];
         __syncthreads();
         tile_setup(a, it, A, base, offs, kTileTC);
         __syncthreads();
         uint8_t* img = out + (size_t)w * sh.set;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int kk = idx & ((1 << LGKE) - 1), b = (idx >> LGKE) & (kTileTC - 1), kg = idx >> (LGKE + 7);
-            const int k = (kg << LGKE) + kk;
-            double v = 0.0;
-            if (b < it.count && k < a.m) v = x[base[b] + offs[k]];
-            else if (b < it.count && k == a.m) v = A.dT;
-            const uint32_t off = (uint32_t)(b >> 3) * sbo + (uint32_t)kg * 128u + (uint32_t)(b & 7) * 16u +
-                                 (uint32_t)kk * ESZ;
-            put<MODE>(img, sh.plane, off, v);
+        const int i0 = (int)((long long)total * c / split), i1 = (int)((long long)total * (c + 1) / split);
+        for (int i = i0 + threadIdx.x; i < i1; i += U * blockDim.x) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = i + u * blockDim.x;
+                const int kk = idx & ((1 << LGKE) - 1), b = (idx >> LGKE) & (kTileTC - 1), kg = idx >> (LGKE + 7);
+                const int k = (kg << LGKE) + kk;
+                v[u] = 0.0;
+                if (idx < i1 && b < it.count && k < a.m) v[u] = x[base[b] + offs[k]];
+                else if (idx < i1 && b < it.count && k == a.m) v[u] = A.dT;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = i + u * blockDim.x;
+                if (idx >= i1) break;
+                const int kk = idx & ((1 << LGKE) - 1), b = (idx >> LGKE) & (kTileTC - 1), kg = idx >> (LGKE + 7);
+                const uint32_t off = (uint32_t)(b >> 3) * sbo + (uint32_t)kg * 128u + (uint32_t)(b & 7) * 16u +
+                                     (uint32_t)kk * ESZ;
+                put<MODE>(img, sh.plane, off, v[u]);
+            }
         }
     }
 }
@@ -139,33 +153,92 @@ struct RecTcArgs {
     int* err;
 };
 
+// The CTA is split in two roles: warp 0 (one thread) issues the bulk copies
+// and the MMAs, warps 1-8 run the epilogue. The epilogue warps synchronise
+// among themselves only (named barrier 1), so the MMAs of the next element tile
+// never wait for the output stores of the previous one.
+constexpr int kRecsThreads = 288;   // 1 + 8 warps
+constexpr int kRecsEpi = 256;
+
+__device__ __forceinline__ bool epi_sync_or(bool pred) {   // named barrier 1 over the epilogue warps
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(kRecsEpi)
+        : "memory");
+    return r != 0;
+}
+
+// Von Mises of one epilogue thread's elements of an accumulated element tile:
+// its block is TMEM lane 32 lg + lane (tl addresses the lane group and the
+// accumulator); half 0 takes elements 0..9 (columns 0..63), half 1 elements
+// 10..20 (columns 48..127). All TMEM reads are issued before one wait.
+__device__ __forceinline__ void epi_vm(uint32_t tl, int half, float* orow) {
+    if (half == 0) {
+        uint32_t r[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tc::tmem_ld16_nw(tl + 16u * c, r[c]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tc::tmem_wait16(r[c]);
+        float v[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
+#pragma unroll
+        for (int e = 0; e < 10; ++e) orow[e] = von_mises6(v + 6 * e);
+    } else {
+        uint32_t r[5][16];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) tc::tmem_ld16_nw(tl + 48u + 16u * c, r[c]);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) tc::tmem_wait16(r[c]);
+        float v[80];
+#pragma unroll
+        for (int c = 0; c < 80; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
+#pragma unroll
+        for (int e = 10; e < kElemPerTile; ++e) orow[e] = von_mises6(v + 6 * e - 48);
+    }
+}
+
+// Output of one element tile from its staging buffer: runs of up to 21
+// consecutive elements per block, consecutive epilogue threads on consecutive
+// elements.
+__device__ __forceinline__ void epi_store(const RecTcArgs& a, const ApplyWork& it, int et, const float* os, int t) {
+    const int el0 = et * kElemPerTile;
+    const int ne = min(kElemPerTile, a.n_el - el0);
+    for (int o = t; o < it.count * kElemPerTile; o += kRecsEpi) {
+        const int b = o / kElemPerTile, e = o - b * kElemPerTile;
+        if (e < ne) a.out[(long long)a.blist[it.start + b] * a.n_el + el0 + e] = os[o];
+    }
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kRecThreads, 1) k_recover_tc(const __grid_constant__ RecTcArgs a,
-                                                                const RecShape sh) {
+__global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tc(const __grid_constant__ RecTcArgs a,
+                                                                 const RecShape sh) {
     constexpr bool TF32 = MODE == MSTRESS_TF32;
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
     constexpr int kTries = 1 << 24;
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sB = smem;              // coefficients of the item's block tile
+    uint8_t* sB = smem;              // coefficients of the current block tile
     uint8_t* sA0 = smem + sh.set;    // S_mean tile stages
-    __shared__ __align__(8) uint64_t bfull, afull[kMaxStages], aempty[kMaxStages], accfull[2], accempty[2];
+    __shared__ __align__(8) uint64_t bfull, bempty, afull[kMaxStages], aempty[kMaxStages], accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ long long eidx[kTileTC];
-    __shared__ float ostage[kTileTC * kElemPerTile];   // von Mises of one element tile, [block][element]
+    __shared__ float ostage[2][kTileTC * kElemPerTile];   // von Mises of an element tile, [block][element]
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int S = sh.stages;
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+    const uint32_t S = (uint32_t)sh.stages;
+    if (warp == 0) tc::tmem_alloc_c<256>(&tmem_base);
     if (tid == 0) {
         tc::mbar_init(&bfull, 1);
-        for (int i = 0; i < S; ++i) {
+        tc::mbar_init(&bempty, 1);
+        for (uint32_t i = 0; i < S; ++i) {
             tc::mbar_init(&afull[i], 1);
             tc::mbar_init(&aempty[i], 1);
         }
         for (int j = 0; j < 2; ++j) {
             tc::mbar_init(&accfull[j], 1);
-            tc::mbar_init(&accempty[j], kRecThreads);
+            tc::mbar_init(&accempty[j], kRecsEpi);
         }
         s_fail = 0;
     }
@@ -173,144 +246,115 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover_tc(const __grid_cons
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tc::instr_desc(TF32, 128, 128);
-    const uint32_t sbo = tc::sbo_bytes(sh.kpad, sh.esz);
-    // epilogue geometry: TMEM lane (= block of the tile) and which elements:
-    // warps 0-3 elements 0..9 (columns 0..63), warps 4-7 elements 10..20 (columns 48..127)
-    const int lg = warp & 3, half = warp >> 2;
-    const int bl = 32 * lg + lane;
-    uint32_t T = 0;                               // element tiles whose MMAs this CTA has issued
-    uint32_t items = 0;                           // work items (coefficient tiles) finished
-    bool ok = true;
     // this CTA's share of the (block tile, element tile) pairs, in block-tile
     // major order: a contiguous range, so every CTA gets the same number of
     // element tiles (+-1) and at most a few coefficient tiles
     const long long n_pairs = (long long)a.n_work * sh.n_etiles;
-    const long long p_end = n_pairs * (blockIdx.x + 1) / gridDim.x;
-    for (long long p = n_pairs * blockIdx.x / gridDim.x; p < p_end;) {
-        const int tw = (int)(p / sh.n_etiles);
-        const int e0 = (int)(p - (long long)tw * sh.n_etiles);
-        const int nt = (int)min((long long)(sh.n_etiles - e0), p_end - p);
-        p += nt;
-        const ApplyWork it = a.work[tw];
-        const uint8_t* simg = a.simg[it.type];
-        __syncthreads();                          // the previous item's epilogue is done with eidx
-        if (tid < kTileTC) eidx[tid] = tid < it.count ? (long long)a.blist[it.start + tid] : -1;
-        if (tid == 0) {
-            // every MMA of the previous item has completed (its last epilogue waited for it)
-            tc::mbar_expect_tx(&bfull, sh.set);
-            tc::bulk_g2s(sB, a.cimg + (size_t)tw * sh.set, sh.set, &bfull);
-            for (int i = 0; i < min(S, nt); ++i) {
-                const uint32_t g = T + i, s = g % S, use = g / S;
-                if (use > 0 && !tc::mbar_wait(&aempty[s], (use - 1) & 1u, kTries)) s_fail = 1;
-                tc::mbar_expect_tx(&afull[s], sh.set);
-                tc::bulk_g2s(sA0 + (size_t)s * sh.set, simg + (size_t)(e0 + i) * sh.set, sh.set, &afull[s]);
-            }
-        }
-        __syncthreads();
-        for (int i = 0; i <= nt; ++i) {
-            if (i < nt && tid == 0 && !s_fail) {   // MMAs of element tile e0 + i
-                const uint32_t g = T + i, s = g % S, j = g & 1u;
-                bool w_ok = true;
-                if (i == 0) w_ok = tc::mbar_wait(&bfull, items & 1u, kTries);
-                if (w_ok && g >= 2) w_ok = tc::mbar_wait(&accempty[j], ((g >> 1) - 1) & 1u, kTries);
-                if (w_ok) w_ok = tc::mbar_wait(&afull[s], (g / S) & 1u, kTries);
+    const long long p0 = n_pairs * blockIdx.x / gridDim.x, p1 = n_pairs * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t n_tiles = (uint32_t)(p1 - p0);
+    if (warp == 0) {
+        if (lane == 0) {
+            auto issue = [&](uint32_t g) {   // the S_mean tile of pair p0 + g into stage g % S
+                const long long pr = p0 + g;
+                const int bt = (int)(pr / sh.n_etiles), et = (int)(pr - (long long)bt * sh.n_etiles);
+                const uint32_t st = g % S;
+                tc::mbar_expect_tx(&afull[st], sh.set);
+                tc::bulk_g2s(sA0 + (size_t)st * sh.set, a.simg[a.work[bt].type] + (size_t)et * sh.set, sh.set,
+                             &afull[st]);
+            };
+            const uint32_t idesc = tc::instr_desc(TF32, 128, 128);
+            const uint32_t sbo = tc::sbo_bytes(sh.kpad, sh.esz);
+            bool ok = true;
+            uint32_t items = 0;   // coefficient tiles loaded
+            for (uint32_t g = 0; g < S && g < n_tiles; ++g) issue(g);
+            int cur_bt = -1;
+            for (uint32_t g = 0; g < n_tiles && ok; ++g) {
+                const int bt = (int)((p0 + g) / sh.n_etiles);
+                const uint32_t j = g & 1u, st = g % S;
+                if (bt != cur_bt) {
+                    // the previous block tile's MMAs have completed before its coefficients are replaced
+                    if (items > 0) ok = tc::mbar_wait(&bempty, (items - 1) & 1u, kTries);
+                    if (!ok) break;
+                    tc::mbar_expect_tx(&bfull, sh.set);
+                    tc::bulk_g2s(sB, a.cimg + (size_t)bt * sh.set, sh.set, &bfull);
+                    ok = tc::mbar_wait(&bfull, items & 1u, kTries);
+                    ++items;
+                    cur_bt = bt;
+                    if (!ok) break;
+                }
+                if (g >= 2) ok = tc::mbar_wait(&accempty[j], ((g >> 1) - 1) & 1u, kTries);
+                if (ok) ok = tc::mbar_wait(&afull[st], (g / S) & 1u, kTries);
                 tc::fence_after();
-                if (w_ok) {
-                    const uint32_t a0 = tc::smem_addr(sA0 + (size_t)s * sh.set), b0 = tc::smem_addr(sB);
-                    uint32_t acc = 0;
-                    for (int ks = 0; ks < sh.ksteps; ++ks) {
-                        const uint32_t ko = (uint32_t)ks * 2 * tc::kLBO;
+                if (!ok) break;
+                const uint32_t a0 = tc::smem_addr(sA0 + (size_t)st * sh.set), b0 = tc::smem_addr(sB);
+                for (int ks = 0; ks < sh.ksteps; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 2 * tc::kLBO;
 #pragma unroll
-                        for (int pr = 0; pr < (NS == 2 ? 3 : 1); ++pr) {
-                            const uint32_t pa = pr == 1 ? sh.plane : 0u, pb = pr == 2 ? sh.plane : 0u;
-                            // M = blocks (coefficients), N = S_mean rows
-                            tc::mma<TF32>(tmem + 128u * j, tc::smem_desc(b0 + pb + ko, tc::kLBO, sbo),
-                                          tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo), idesc, acc);
-                            acc = 1;
-                        }
-                    }
-                    tc::commit(&accfull[j]);
-                    tc::commit(&aempty[s]);
-                    if (S >= 2 && i >= 1 && i - 1 + S < nt) {
-                        // refill the stage of the previous tile (its MMAs have had a tile's time)
-                        const uint32_t gp = g - 1, sp = gp % S;
-                        w_ok = tc::mbar_wait(&aempty[sp], (gp / S) & 1u, kTries);
-                        if (w_ok) {
-                            tc::mbar_expect_tx(&afull[sp], sh.set);
-                            tc::bulk_g2s(sA0 + (size_t)sp * sh.set, simg + (size_t)(e0 + i - 1 + S) * sh.set,
-                                         sh.set, &afull[sp]);
-                        }
-                    } else if (S == 1 && i + 1 < nt) {
-                        // a single stage: wait for this tile's MMAs, then fetch the next tile
-                        w_ok = tc::mbar_wait(&aempty[0], g & 1u, kTries);
-                        if (w_ok) {
-                            tc::mbar_expect_tx(&afull[0], sh.set);
-                            tc::bulk_g2s(sA0, simg + (size_t)(e0 + i + 1) * sh.set, sh.set, &afull[0]);
-                        }
+                    for (int pr = 0; pr < (NS == 2 ? 3 : 1); ++pr) {
+                        const uint32_t pa = pr == 1 ? sh.plane : 0u, pb = pr == 2 ? sh.plane : 0u;
+                        // M = blocks (coefficients), N = S_mean rows
+                        tc::mma<TF32>(tmem + 128u * j, tc::smem_desc(b0 + pb + ko, tc::kLBO, sbo),
+                                      tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo), idesc,
+                                      (ks > 0 || pr > 0) ? 1u : 0u);
                     }
                 }
-                if (!w_ok) s_fail = 1;
-            }
-            if (i >= 1) {   // epilogue of element tile e0 + i - 1
-                const uint32_t g = T + i - 1, j = g & 1u;
-                const bool got = !s_fail && tc::mbar_wait(&accfull[j], (g >> 1) & 1u, kTries);
-                tc::fence_after();
-                if (got) {
-                    const uint32_t tl = tmem + ((uint32_t)(32 * lg) << 16) + 128u * j;
-                    float* orow = ostage + bl * kElemPerTile;
-                    if (half == 0) {
-                        float v[64];
-#pragma unroll
-                        for (int c = 0; c < 64; c += 16) tc::tmem_ld16(tl + (uint32_t)c, v + c);
-#pragma unroll
-                        for (int e = 0; e < 10; ++e) orow[e] = von_mises6(v + 6 * e);
-                    } else {
-                        float v[80];
-#pragma unroll
-                        for (int c = 0; c < 80; c += 16) tc::tmem_ld16(tl + 48u + (uint32_t)c, v + c);
-#pragma unroll
-                        for (int e = 10; e < kElemPerTile; ++e) orow[e] = von_mises6(v + 6 * e - 48);
+                tc::commit(&accfull[j]);
+                tc::commit(&aempty[st]);
+                if (g + 1 == n_tiles || (int)((p0 + g + 1) / sh.n_etiles) != bt) tc::commit(&bempty);
+                if (S == 1) {
+                    // a single stage: this tile's MMAs finish before the next tile is fetched
+                    if (g + 1 < n_tiles) {
+                        ok = tc::mbar_wait(&aempty[0], g & 1u, kTries);
+                        if (ok) issue(g + 1);
                     }
-                } else {
-                    s_fail = 1;
-                }
-                tc::fence_before();
-                tc::mbar_arrive(&accempty[j]);
-                __syncthreads();
-                // runs of up to 21 consecutive elements per block
-                const int el0 = (e0 + i - 1) * kElemPerTile;
-                const int ne = min(kElemPerTile, a.n_el - el0);
-                for (int o = tid; o < it.count * kElemPerTile; o += kRecThreads) {
-                    const int b = o / kElemPerTile, e = o - b * kElemPerTile;
-                    if (e < ne) a.out[eidx[b] * a.n_el + el0 + e] = ostage[o];
+                } else if (g >= 1 && g - 1 + S < n_tiles) {
+                    // refill the previous tile's stage (its MMAs have had a tile's time)
+                    const uint32_t sp = (g - 1) % S;
+                    ok = tc::mbar_wait(&aempty[sp], ((g - 1) / S) & 1u, kTries);
+                    if (ok) issue(g - 1 + S);
                 }
             }
-            if (__syncthreads_or(s_fail)) {
-                ok = false;
-                break;
-            }
+            if (!ok) *(volatile int*)&s_fail = 1;
         }
-        if (!ok) break;
-        T += nt;
-        ++items;
+    } else {
+        // ---------------- epilogue: blocks on TMEM lanes, one element tile at a time
+        const int t = tid - 32;                           // 0..255
+        const int lg = warp & 3, half = (warp - 1) >> 2;  // warps 1-4: elements 0..9, warps 5-8: 10..20
+        const int bl = 32 * lg + lane;
+        for (uint32_t g = 0; g < n_tiles; ++g) {
+            const uint32_t j = g & 1u;
+            const long long pr = p0 + g;
+            const int bt = (int)(pr / sh.n_etiles), et = (int)(pr - (long long)bt * sh.n_etiles);
+            bool got = !*(volatile int*)&s_fail && tc::mbar_wait(&accfull[j], (g >> 1) & 1u, kTries);
+            got = __all_sync(0xffffffffu, got);   // the TMEM reads are warp-collective
+            tc::fence_after();
+            float* os = ostage[j];
+            if (got) epi_vm(tmem + ((uint32_t)(32 * lg) << 16) + 128u * j, half, os + bl * kElemPerTile);
+            else *(volatile int*)&s_fail = 1;
+            tc::fence_before();
+            tc::mbar_arrive(&accempty[j]);
+            // one barrier per tile: the stages alternate, and a thread writes stage j
+            // again only after every thread has passed the next tile's barrier
+            if (epi_sync_or(!got)) break;
+            epi_store(a, a.work[bt], et, os, t);
+        }
     }
-    if (!ok && tid == 0) {
+    __syncthreads();
+    if (tid == 0 && s_fail) {
         atomicExch(a.err, 1);
         // bounded drain: let issued copies and MMAs finish before the CTA leaves
-        tc::mbar_wait(&bfull, (items & 1u), 1 << 20);
-        for (int s = 0; s < S; ++s) {
-            tc::mbar_wait(&afull[s], 0, 1 << 16);
-            tc::mbar_wait(&afull[s], 1, 1 << 16);
-        }
-        for (int j = 0; j < 2; ++j) {
-            tc::mbar_wait(&accfull[j], 0, 1 << 16);
-            tc::mbar_wait(&accfull[j], 1, 1 << 16);
+        for (uint32_t par = 0; par < 2; ++par) {
+            tc::mbar_wait(&bfull, par, 1 << 16);
+            tc::mbar_wait(&bempty, par, 1 << 16);
+            for (uint32_t i = 0; i < S; ++i) {
+                tc::mbar_wait(&afull[i], par, 1 << 16);
+                tc::mbar_wait(&aempty[i], par, 1 << 16);
+            }
         }
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, 256);
+    if (warp == 0) tc::tmem_free_c<256>(tmem);
 }
 
 // ----------------------------------------------------------- streamed K
@@ -323,9 +367,6 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover_tc(const __grid_cons
 // Barriers: full[s] (both copies' bytes), empty[s] (tcgen05.commit after the
 // slot's MMAs), accfull[j] (commit after an element tile's last slot) and
 // accempty[j] (the 256 epilogue threads arrive when the accumulator is read).
-constexpr int kRecsThreads = 288;   // 1 + 8 warps
-constexpr int kRecsEpi = 256;
-
 struct RecsShape {
     int m1, esz, ns, kc, nks, kpad, n_etiles, stages;
     uint32_t plane;                  // bytes of one 128 x kc plane of a slot
@@ -384,25 +425,27 @@ __global__ void k_coeff_image_s(const __grid_constant__ ApplyArgs a, RecsShape s
         __syncthreads();
         tile_setup(a, it, A, base, offs, kTileTC);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int b = idx / sh.kpad, k = idx - b * sh.kpad;   // consecutive threads: one row's K values
-            double v = 0.0;
-            if (b < it.count && k < a.m) v = x[base[b] + offs[k]];
-            else if (b < it.count && k == a.m) v = A.dT;
-            const uint32_t o = tc::operand_offset(b, k % sh.kc, sh.kc, sh.esz);
-            put<MODE>(out + slot_offset(sh, w, b, k) - o, sh.plane, o, v);
+        constexpr int U = 4;   // loads in flight per thread
+        for (int i = threadIdx.x; i < total; i += U * blockDim.x) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = i + u * blockDim.x;
+                const int b = idx / sh.kpad, k = idx - b * sh.kpad;   // consecutive threads: one row's K values
+                v[u] = 0.0;
+                if (idx < total && b < it.count && k < a.m) v[u] = x[base[b] + offs[k]];
+                else if (idx < total && b < it.count && k == a.m) v[u] = A.dT;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = i + u * blockDim.x;
+                if (idx >= total) break;
+                const int b = idx / sh.kpad, k = idx - b * sh.kpad;
+                const uint32_t o = tc::operand_offset(b, k % sh.kc, sh.kc, sh.esz);
+                put<MODE>(out + slot_offset(sh, w, b, k) - o, sh.plane, o, v[u]);
+            }
         }
     }
-}
-
-__device__ __forceinline__ bool epi_sync_or(bool pred) {   // named barrier 1 over the epilogue warps
-    uint32_t r;
-    asm volatile(
-        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "n"(kRecsEpi)
-        : "memory");
-    return r != 0;
 }
 
 template <int MODE>
@@ -415,7 +458,7 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full[4], empty[4], accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ float ostage[kTileTC * kElemPerTile];
+    __shared__ float ostage[2][kTileTC * kElemPerTile];
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t S = (uint32_t)sh.stages;
@@ -492,45 +535,24 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
         }
     } else {
         // ---------------- epilogue: blocks on TMEM lanes, one element tile at a time
-        const int et_id = tid - 32;                       // 0..255
+        const int t = tid - 32;                           // 0..255
         const int lg = warp & 3, half = (warp - 1) >> 2;  // warps 1-4: elements 0..9, warps 5-8: 10..20
         const int bl = 32 * lg + lane;
         for (uint32_t g = 0; g < n_tiles; ++g) {
             const uint32_t j = g & 1u;
             const long long pr = p0 + g;
             const int bt = (int)(pr / sh.n_etiles), et = (int)(pr - (long long)bt * sh.n_etiles);
-            const bool got = !*(volatile int*)&s_fail && tc::mbar_wait(&accfull[j], (g >> 1) & 1u, kTries);
+            bool got = !*(volatile int*)&s_fail && tc::mbar_wait(&accfull[j], (g >> 1) & 1u, kTries);
+            got = __all_sync(0xffffffffu, got);   // the TMEM reads are warp-collective
             tc::fence_after();
-            if (got) {
-                const uint32_t tl = tmem + ((uint32_t)(32 * lg) << 16) + 128u * j;
-                float* orow = ostage + bl * kElemPerTile;
-                if (half == 0) {
-                    float v[64];
-#pragma unroll
-                    for (int c = 0; c < 64; c += 16) tc::tmem_ld16(tl + (uint32_t)c, v + c);
-#pragma unroll
-                    for (int e = 0; e < 10; ++e) orow[e] = von_mises6(v + 6 * e);
-                } else {
-                    float v[80];
-#pragma unroll
-                    for (int c = 0; c < 80; c += 16) tc::tmem_ld16(tl + 48u + (uint32_t)c, v + c);
-#pragma unroll
-                    for (int e = 10; e < kElemPerTile; ++e) orow[e] = von_mises6(v + 6 * e - 48);
-                }
-            } else {
-                *(volatile int*)&s_fail = 1;
-            }
+            float* os = ostage[j];
+            if (got) epi_vm(tmem + ((uint32_t)(32 * lg) << 16) + 128u * j, half, os + bl * kElemPerTile);
+            else *(volatile int*)&s_fail = 1;
             tc::fence_before();
             tc::mbar_arrive(&accempty[j]);
+            // one barrier per tile (alternating stages, as in k_recover_tc)
             if (epi_sync_or(!got)) break;
-            const ApplyWork it = a.work[bt];
-            const int el0 = et * kElemPerTile;
-            const int ne = min(kElemPerTile, a.n_el - el0);
-            for (int o = et_id; o < it.count * kElemPerTile; o += kRecsEpi) {
-                const int b = o / kElemPerTile, e = o - b * kElemPerTile;
-                if (e < ne) a.out[(long long)a.blist[it.start + b] * a.n_el + el0 + e] = ostage[o];
-            }
-            epi_sync_or(false);   // the stage is read before the next tile's epilogue writes it
+            epi_store(a, a.work[bt], et, os, t);
         }
     }
     __syncthreads();
@@ -659,12 +681,14 @@ void recover_vm_tc(mstress_sol_s* s, float* out) {
     ApplyArgs aa = apply_args(s, s->v64.x.ptr, nullptr, nullptr, nullptr, true);
     aa.work = s->d_awork_rec.as<ApplyWork>();   // 128-block tiles
     aa.n_work = s->n_awork_rec;
-    const int gi = std::max(1, std::min(s->n_awork_rec, ctx->num_sms * 8));
+    // a few CTAs per tile when there are few tiles, so that every SM gathers
+    const int split = std::max(1, std::min(8, (4 * ctx->num_sms + s->n_awork_rec - 1) / std::max(1, s->n_awork_rec)));
+    const int gi = std::max(1, std::min(s->n_awork_rec * split, ctx->num_sms * 8));
     uint8_t* cimg = s->cimg.as<uint8_t>();
     switch (prec) {
-        case MSTRESS_TF32: k_coeff_image<MSTRESS_TF32><<<gi, 256, 0, ctx->stream>>>(aa, sh, cimg); break;
-        case MSTRESS_BF16: k_coeff_image<MSTRESS_BF16><<<gi, 256, 0, ctx->stream>>>(aa, sh, cimg); break;
-        default: k_coeff_image<MSTRESS_BF16X3><<<gi, 256, 0, ctx->stream>>>(aa, sh, cimg); break;
+        case MSTRESS_TF32: k_coeff_image<MSTRESS_TF32><<<gi, 256, 0, ctx->stream>>>(aa, sh, split, cimg); break;
+        case MSTRESS_BF16: k_coeff_image<MSTRESS_BF16><<<gi, 256, 0, ctx->stream>>>(aa, sh, split, cimg); break;
+        default: k_coeff_image<MSTRESS_BF16X3><<<gi, 256, 0, ctx->stream>>>(aa, sh, split, cimg); break;
     }
     MS_LAUNCH_CHECK();
     RecTcArgs ra;
@@ -683,9 +707,9 @@ void recover_vm_tc(mstress_sol_s* s, float* out) {
     const long long pairs = (long long)s->n_awork_rec * sh.n_etiles;
     const int grid = (int)std::max(1LL, std::min(pairs, (long long)ctx->num_sms));
     switch (prec) {
-        case MSTRESS_TF32: k_recover_tc<MSTRESS_TF32><<<grid, kRecThreads, sh.smem, ctx->stream>>>(ra, sh); break;
-        case MSTRESS_BF16: k_recover_tc<MSTRESS_BF16><<<grid, kRecThreads, sh.smem, ctx->stream>>>(ra, sh); break;
-        default: k_recover_tc<MSTRESS_BF16X3><<<grid, kRecThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        case MSTRESS_TF32: k_recover_tc<MSTRESS_TF32><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        case MSTRESS_BF16: k_recover_tc<MSTRESS_BF16><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        default: k_recover_tc<MSTRESS_BF16X3><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
     }
     MS_LAUNCH_CHECK();
 }
