@@ -36,6 +36,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// 128-byte swizzled K-major layout (the other operand layout used here): rows
+// of 128 bytes of K, eight rows form a 1024-byte atom (atoms 1024-byte aligned
+// and SBO = 1024 bytes apart along M/N), and the 16-byte chunk c of row r is
+// stored at chunk position c ^ (r % 8), so the eight rows of a core matrix
+// fall in different bank groups. One MMA consumes 32 bytes of a row; the K
+// steps within a row advance the descriptor start address by 32 bytes (the
+// hardware applies the XOR to the address bits).
+constexpr uint32_t kSw128Atom = 1024;
+
+__host__ __device__ inline uint32_t sw128_offset(int row, int kbyte) {
+    return (uint32_t)(row >> 3) * kSw128Atom + (uint32_t)(row & 7) * 128u +
+           ((uint32_t)(((kbyte >> 4) ^ (row & 7)) & 7) << 4) + (uint32_t)(kbyte & 15);
+}
+
+// Descriptor of a 128-byte swizzled K-major operand: SBO = 1024 bytes, layout
+// type 2 (128-byte swizzle) in bits 61-63, version 1, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)((kSw128Atom >> 4) & 0x3FFF) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B formats
 // (bits 7-9, 10-12: 1 = bf16 for kind::f16, 2 = tf32 for kind::tf32), both
 // K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.

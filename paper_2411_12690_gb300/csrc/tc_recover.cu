@@ -149,16 +149,18 @@ struct RecTcArgs {
     const uint8_t* cimg;            // coefficient images, one per block tile
     const uint8_t* simg[kMaxTypes]; // S_mean tile images per type
     int n_el;
+    int n_seg;                      // streamed recovery: element-tile segments per block tile
     float* out;                     // [block][n_el]
     int* err;
 };
 
 // The CTA is split in two roles: warp 0 (one thread) issues the bulk copies
-// and the MMAs, warps 1-8 run the epilogue. The epilogue warps synchronise
+// and the MMAs, warps 1-16 run the epilogue. The epilogue warps synchronise
 // among themselves only (named barrier 1), so the MMAs of the next element tile
 // never wait for the output stores of the previous one.
-constexpr int kRecsThreads = 288;   // 1 + 8 warps
-constexpr int kRecsEpi = 256;
+constexpr int kRecsEpiWarps = 16;                 // four per TMEM lane group
+constexpr int kRecsEpi = 32 * kRecsEpiWarps;      // epilogue threads
+constexpr int kRecsThreads = 32 + kRecsEpi;       // + the copy / MMA warp
 
 __device__ __forceinline__ bool epi_sync_or(bool pred) {   // named barrier 1 over the epilogue warps
     uint32_t r;
@@ -170,46 +172,77 @@ __device__ __forceinline__ bool epi_sync_or(bool pred) {   // named barrier 1 ov
     return r != 0;
 }
 
-// Von Mises of one epilogue thread's elements of an accumulated element tile:
-// its block is TMEM lane 32 lg + lane (tl addresses the lane group and the
-// accumulator); half 0 takes elements 0..9 (columns 0..63), half 1 elements
-// 10..20 (columns 48..127). All TMEM reads are issued before one wait.
-__device__ __forceinline__ void epi_vm(uint32_t tl, int half, float* orow) {
-    if (half == 0) {
-        uint32_t r[4][16];
+// Von Mises of one epilogue thread's elements of an accumulated element tile.
+// Its block is TMEM lane 32 lg + lane (tl addresses the lane group and the
+// accumulator); the four epilogue warps of a lane group split the 21 elements
+// as 0-4, 5-9, 10-15, 16-20 (columns 0-29, 30-59, 60-95, 96-125, read in
+// 16-column groups starting at C0). All TMEM reads are issued before one wait.
+template <int C0, int N16, int E0, int E1>
+__device__ __forceinline__ void epi_part(uint32_t tl, float* orow) {
+    uint32_t r[N16][16];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tc::tmem_ld16_nw(tl + 16u * c, r[c]);
+    for (int c = 0; c < N16; ++c) tc::tmem_ld16_nw(tl + (uint32_t)(C0 + 16 * c), r[c]);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tc::tmem_wait16(r[c]);
-        float v[64];
+    for (int c = 0; c < N16; ++c) tc::tmem_wait16(r[c]);
+    float v[16 * N16];
 #pragma unroll
-        for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
+    for (int c = 0; c < 16 * N16; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
 #pragma unroll
-        for (int e = 0; e < 10; ++e) orow[e] = von_mises6(v + 6 * e);
-    } else {
-        uint32_t r[5][16];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) tc::tmem_ld16_nw(tl + 48u + 16u * c, r[c]);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) tc::tmem_wait16(r[c]);
-        float v[80];
-#pragma unroll
-        for (int c = 0; c < 80; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
-#pragma unroll
-        for (int e = 10; e < kElemPerTile; ++e) orow[e] = von_mises6(v + 6 * e - 48);
+    for (int e = E0; e < E1; ++e) orow[e] = von_mises6(v + 6 * e - C0);
+}
+
+__device__ __forceinline__ void epi_vm(uint32_t tl, int part, float* orow) {
+    switch (part) {
+        case 0: epi_part<0, 2, 0, 5>(tl, orow); break;
+        case 1: epi_part<16, 3, 5, 10>(tl, orow); break;
+        case 2: epi_part<48, 3, 10, 16>(tl, orow); break;
+        default: epi_part<96, 2, 16, kElemPerTile>(tl, orow); break;
     }
 }
 
-// Output of one element tile from its staging buffer: runs of up to 21
-// consecutive elements per block, consecutive epilogue threads on consecutive
-// elements.
-__device__ __forceinline__ void epi_store(const RecTcArgs& a, const ApplyWork& it, int et, const float* os, int t) {
+// Epilogue state across tiles: the block tile being written, its block count,
+// and which of the two row-offset buffers holds its output rows.
+struct EpiRows {
+    int bt = -1, count = 0, buf = 1;
+};
+
+// Called by every epilogue thread (t = 0..kRecsEpi-1) before the tile's
+// barrier: on a new block tile, fill the other row-offset buffer (the one
+// used two block tiles ago; every thread passed a barrier since its last use).
+__device__ __forceinline__ void epi_rows(const RecTcArgs& a, int bt, int t, long long (*rowoff)[kTileTC],
+                                         EpiRows& er) {
+    if (bt == er.bt) return;
+    const ApplyWork it = a.work[bt];
+    er.bt = bt;
+    er.count = it.count;
+    er.buf ^= 1;
+    if (t < kTileTC) rowoff[er.buf][t] = t < it.count ? (long long)a.blist[it.start + t] * a.n_el : 0;
+}
+
+// Output of one element tile from its staging buffer, after the tile's
+// barrier: runs of up to 21 consecutive elements per block, consecutive
+// threads on consecutive elements; all staging reads before the stores.
+__device__ __forceinline__ void epi_store(const RecTcArgs& a, const EpiRows& er, const long long* rowoff, int et,
+                                          const float* os, int t) {
+    constexpr int kIt = (kTileTC * kElemPerTile + kRecsEpi - 1) / kRecsEpi;
     const int el0 = et * kElemPerTile;
     const int ne = min(kElemPerTile, a.n_el - el0);
-    for (int o = t; o < it.count * kElemPerTile; o += kRecsEpi) {
+    const int n = er.count * kElemPerTile;
+    float v[kIt];
+    long long ad[kIt];
+#pragma unroll
+    for (int i = 0; i < kIt; ++i) {
+        const int o = t + i * kRecsEpi;
         const int b = o / kElemPerTile, e = o - b * kElemPerTile;
-        if (e < ne) a.out[(long long)a.blist[it.start + b] * a.n_el + el0 + e] = os[o];
+        ad[i] = -1;
+        if (o < n && e < ne) {
+            v[i] = os[o];
+            ad[i] = rowoff[b] + el0 + e;
+        }
     }
+#pragma unroll
+    for (int i = 0; i < kIt; ++i)
+        if (ad[i] >= 0) a.out[ad[i]] = v[i];
 }
 
 template <int MODE>
@@ -225,6 +258,7 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tc(const __grid_con
     __shared__ __align__(8) uint64_t bfull, bempty, afull[kMaxStages], aempty[kMaxStages], accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ float ostage[2][kTileTC * kElemPerTile];   // von Mises of an element tile, [block][element]
+    __shared__ long long rowoff[2][kTileTC];               // output row offsets of the block tile's blocks
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t S = (uint32_t)sh.stages;
@@ -318,25 +352,27 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tc(const __grid_con
         }
     } else {
         // ---------------- epilogue: blocks on TMEM lanes, one element tile at a time
-        const int t = tid - 32;                           // 0..255
-        const int lg = warp & 3, half = (warp - 1) >> 2;  // warps 1-4: elements 0..9, warps 5-8: 10..20
+        const int t = tid - 32;                            // 0..kRecsEpi-1
+        const int lg = warp & 3, part = (warp - 1) >> 2;   // lane group, element part
         const int bl = 32 * lg + lane;
+        EpiRows er;
         for (uint32_t g = 0; g < n_tiles; ++g) {
             const uint32_t j = g & 1u;
             const long long pr = p0 + g;
             const int bt = (int)(pr / sh.n_etiles), et = (int)(pr - (long long)bt * sh.n_etiles);
+            epi_rows(a, bt, t, rowoff, er);
             bool got = !*(volatile int*)&s_fail && tc::mbar_wait(&accfull[j], (g >> 1) & 1u, kTries);
             got = __all_sync(0xffffffffu, got);   // the TMEM reads are warp-collective
             tc::fence_after();
             float* os = ostage[j];
-            if (got) epi_vm(tmem + ((uint32_t)(32 * lg) << 16) + 128u * j, half, os + bl * kElemPerTile);
+            if (got) epi_vm(tmem + ((uint32_t)(32 * lg) << 16) + 128u * j, part, os + bl * kElemPerTile);
             else *(volatile int*)&s_fail = 1;
             tc::fence_before();
             tc::mbar_arrive(&accempty[j]);
             // one barrier per tile: the stages alternate, and a thread writes stage j
             // again only after every thread has passed the next tile's barrier
             if (epi_sync_or(!got)) break;
-            epi_store(a, a.work[bt], et, os, t);
+            epi_store(a, er, rowoff[er.buf], et, os, t);
         }
     }
     __syncthreads();
@@ -359,14 +395,15 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tc(const __grid_con
 
 // ----------------------------------------------------------- streamed K
 // Large bases (the coefficient tile does not fit in shared memory next to an
-// S_mean stage): both operands stream along K in slots of kc values (two MMA K
-// steps, 64 bytes of K per row). Both images are stored slot by slot (per
-// tile, per slot, per plane a 128 x kc K-major no-swizzle block), so that one
-// slot of each operand is one bulk copy. The CTA is split in two roles: warp 0
-// (one thread) issues the copies and the MMAs, warps 1-8 run the epilogue.
+// S_mean stage): both operands stream along K in slots of kc values (128 bytes
+// of K per row, four MMA K steps). Both images are stored slot by slot (per
+// tile, per slot, per plane a 128 x kc K-major block in the 128-byte swizzled
+// layout, which the tensor cores read without shared-memory bank conflicts),
+// so that one slot of each operand is one bulk copy. The CTA is split in two roles: warp 0
+// (one thread) issues the copies and the MMAs, warps 1-16 run the epilogue.
 // Barriers: full[s] (both copies' bytes), empty[s] (tcgen05.commit after the
 // slot's MMAs), accfull[j] (commit after an element tile's last slot) and
-// accempty[j] (the 256 epilogue threads arrive when the accumulator is read).
+// accempty[j] (the epilogue threads arrive when the accumulator is read).
 struct RecsShape {
     int m1, esz, ns, kc, nks, kpad, n_etiles, stages;
     uint32_t plane;                  // bytes of one 128 x kc plane of a slot
@@ -379,7 +416,7 @@ RecsShape recs_shape(int m1, int n_el, int prec) {
     s.m1 = m1;
     s.esz = prec == MSTRESS_TF32 ? 4 : 2;
     s.ns = prec == MSTRESS_BF16X3 ? 2 : 1;
-    s.kc = 64 / s.esz;
+    s.kc = 128 / s.esz;                      // one 128-byte swizzle row of K per slot
     s.nks = (m1 + s.kc - 1) / s.kc;
     s.kpad = s.nks * s.kc;
     s.n_etiles = (n_el + kElemPerTile - 1) / kElemPerTile;
@@ -391,9 +428,13 @@ RecsShape recs_shape(int m1, int n_el, int prec) {
 }
 
 // Byte offset of element (row, k) of tile t in a slot-by-slot image.
-__device__ __forceinline__ size_t slot_offset(const RecsShape& sh, long long t, int row, int k) {
-    const int ks = k / sh.kc, kk = k - ks * sh.kc;
-    return ((size_t)t * sh.nks + ks) * sh.slot + tc::operand_offset(row, kk, sh.kc, sh.esz);
+// Byte offset of slot ks of tile t in a slot-by-slot image, and of element
+// (row, kk) within one plane of a slot (128-byte swizzled K-major).
+__device__ __forceinline__ size_t slot_base(const RecsShape& sh, long long t, int ks) {
+    return ((size_t)t * sh.nks + ks) * sh.slot;
+}
+__device__ __forceinline__ uint32_t in_slot(const RecsShape& sh, int row, int kk) {
+    return tc::sw128_offset(row, kk * sh.esz);
 }
 
 template <int MODE>
@@ -409,8 +450,7 @@ __global__ void k_smean_image_s(const double* Smean, int ld, int m1, int n_el, R
     const long long el = tile * kElemPerTile + le;
     double v = 0.0;
     if (le < kElemPerTile && el < n_el && k < m1) v = Smean[((size_t)el * 6 + c) * ld + k];
-    put<MODE>(out + slot_offset(sh, tile, r, k) - tc::operand_offset(r, k % sh.kc, sh.kc, sh.esz),
-              sh.plane, tc::operand_offset(r, k % sh.kc, sh.kc, sh.esz), v);
+    put<MODE>(out + slot_base(sh, tile, k / sh.kc), sh.plane, in_slot(sh, r, k % sh.kc), v);
 }
 
 template <int MODE>
@@ -441,12 +481,33 @@ __global__ void k_coeff_image_s(const __grid_constant__ ApplyArgs a, RecsShape s
                 const int idx = i + u * blockDim.x;
                 if (idx >= total) break;
                 const int b = idx / sh.kpad, k = idx - b * sh.kpad;
-                const uint32_t o = tc::operand_offset(b, k % sh.kc, sh.kc, sh.esz);
-                put<MODE>(out + slot_offset(sh, w, b, k) - o, sh.plane, o, v[u]);
+                put<MODE>(out + slot_base(sh, w, k / sh.kc), sh.plane, in_slot(sh, b, k % sh.kc), v[u]);
             }
         }
     }
 }
+
+// Tile order of the streamed recovery. The units are (block tile, segment of
+// the element tiles), u = bt * n_seg + seg; CTA c takes units c, c + G, c + 2G,
+// ... (G CTAs) and sweeps each unit's element tiles in order. The CTAs of one
+// round thus walk the same S_mean tiles at about the same time, so a tile
+// comes from DRAM once per round and from L2 for the others, and each CTA's
+// coefficient tile stays in L2 for a whole sweep. n_seg > 1 only when there are
+// too few block tiles to keep every CTA busy.
+struct UnitCursor {
+    long long u;
+    int bt, e, e1;
+    __device__ __forceinline__ void begin(long long u_, int n_seg, int n_et) {
+        u = u_;
+        bt = (int)(u / n_seg);
+        const int sg = (int)(u - (long long)bt * n_seg);
+        e = (int)((long long)n_et * sg / n_seg);
+        e1 = (int)((long long)n_et * (sg + 1) / n_seg);
+    }
+    __device__ __forceinline__ void next(int n_seg, int n_et) {
+        if (++e >= e1) begin(u + gridDim.x, n_seg, n_et);
+    }
+};
 
 template <int MODE>
 __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_constant__ RecTcArgs a,
@@ -459,6 +520,7 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
     __shared__ __align__(8) uint64_t full[4], empty[4], accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ float ostage[2][kTileTC * kElemPerTile];
+    __shared__ long long rowoff[2][kTileTC];
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t S = (uint32_t)sh.stages;
@@ -478,17 +540,24 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    // this CTA's contiguous range of (block tile, element tile) pairs, block-tile major
-    const long long n_pairs = (long long)a.n_work * sh.n_etiles;
-    const long long p0 = n_pairs * blockIdx.x / gridDim.x, p1 = n_pairs * (blockIdx.x + 1) / gridDim.x;
-    const uint32_t n_tiles = (uint32_t)(p1 - p0), n_slots = n_tiles * (uint32_t)sh.nks;
+    // this CTA's element tiles, unit by unit (UnitCursor)
+    const int n_seg = a.n_seg;
+    const long long n_units = (long long)a.n_work * n_seg;
+    uint32_t n_tiles = 0;
+    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int sg = (int)(u % n_seg);
+        n_tiles += (uint32_t)((long long)sh.n_etiles * (sg + 1) / n_seg - (long long)sh.n_etiles * sg / n_seg);
+    }
+    const uint32_t n_slots = n_tiles * (uint32_t)sh.nks;
     if (warp == 0) {
         if (lane == 0) {
-            // the copies of global slot q: pair p0 + q / nks, K slot q % nks
+            // the copies of slot q = tile q / nks, K slot q % nks (issued in increasing q)
+            UnitCursor ic;
+            ic.begin(blockIdx.x, n_seg, sh.n_etiles);
             auto issue = [&](uint32_t q) {
-                const long long pr = p0 + q / sh.nks;
                 const int ks = (int)(q % sh.nks);
-                const int bt = (int)(pr / sh.n_etiles), et = (int)(pr - (long long)bt * sh.n_etiles);
+                if (ks == 0 && q > 0) ic.next(n_seg, sh.n_etiles);
+                const int bt = ic.bt, et = ic.e;
                 const uint32_t s = q % S;
                 uint8_t* dst = smem + (size_t)s * 2 * sh.slot;
                 tc::mbar_expect_tx(&full[s], 2 * sh.slot);
@@ -496,7 +565,7 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
                 tc::bulk_g2s(dst + sh.slot, a.cimg + ((size_t)bt * sh.nks + ks) * sh.slot, sh.slot, &full[s]);
             };
             const uint32_t idesc = tc::instr_desc(TF32, 128, 128);
-            const uint32_t sbo = tc::sbo_bytes(sh.kc, sh.esz);
+
             bool ok = true;
             for (uint32_t q = 0; q < S && q < n_slots; ++q) issue(q);
             for (uint32_t g = 0; g < n_tiles && ok; ++g) {
@@ -510,15 +579,15 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
                     const uint32_t a0 = tc::smem_addr(smem + (size_t)s * 2 * sh.slot);   // S_mean slot
                     const uint32_t b0 = a0 + sh.slot;                                   // coefficient slot
 #pragma unroll
-                    for (int kj = 0; kj < 2; ++kj) {
-                        const uint32_t ko = (uint32_t)kj * 2 * tc::kLBO;
+                    for (int kj = 0; kj < 4; ++kj) {   // four 32-byte K steps per 128-byte row
+                        const uint32_t ko = (uint32_t)kj * 32u;
 #pragma unroll
                         for (int pr = 0; pr < (NS == 2 ? 3 : 1); ++pr) {
                             const uint32_t pa = pr == 1 ? sh.plane : 0u, pb = pr == 2 ? sh.plane : 0u;
                             const uint32_t acc = (ks > 0 || kj > 0 || pr > 0) ? 1u : 0u;
                             // M = blocks (coefficients), N = S_mean rows
-                            tc::mma<TF32>(tmem + 128u * j, tc::smem_desc(b0 + pb + ko, tc::kLBO, sbo),
-                                          tc::smem_desc(a0 + pa + ko, tc::kLBO, sbo), idesc, acc);
+                            tc::mma<TF32>(tmem + 128u * j, tc::smem_desc_sw128(b0 + pb + ko),
+                                          tc::smem_desc_sw128(a0 + pa + ko), idesc, acc);
                         }
                     }
                     tc::commit(&empty[s]);
@@ -535,24 +604,28 @@ __global__ void __launch_bounds__(kRecsThreads, 1) k_recover_tcs(const __grid_co
         }
     } else {
         // ---------------- epilogue: blocks on TMEM lanes, one element tile at a time
-        const int t = tid - 32;                           // 0..255
-        const int lg = warp & 3, half = (warp - 1) >> 2;  // warps 1-4: elements 0..9, warps 5-8: 10..20
+        const int t = tid - 32;                            // 0..kRecsEpi-1
+        const int lg = warp & 3, part = (warp - 1) >> 2;   // lane group, element part
         const int bl = 32 * lg + lane;
+        UnitCursor ec;
+        ec.begin(blockIdx.x, n_seg, sh.n_etiles);
+        EpiRows er;
         for (uint32_t g = 0; g < n_tiles; ++g) {
             const uint32_t j = g & 1u;
-            const long long pr = p0 + g;
-            const int bt = (int)(pr / sh.n_etiles), et = (int)(pr - (long long)bt * sh.n_etiles);
+            if (g > 0) ec.next(n_seg, sh.n_etiles);
+            const int bt = ec.bt, et = ec.e;
+            epi_rows(a, bt, t, rowoff, er);
             bool got = !*(volatile int*)&s_fail && tc::mbar_wait(&accfull[j], (g >> 1) & 1u, kTries);
             got = __all_sync(0xffffffffu, got);   // the TMEM reads are warp-collective
             tc::fence_after();
             float* os = ostage[j];
-            if (got) epi_vm(tmem + ((uint32_t)(32 * lg) << 16) + 128u * j, half, os + bl * kElemPerTile);
+            if (got) epi_vm(tmem + ((uint32_t)(32 * lg) << 16) + 128u * j, part, os + bl * kElemPerTile);
             else *(volatile int*)&s_fail = 1;
             tc::fence_before();
             tc::mbar_arrive(&accempty[j]);
             // one barrier per tile (alternating stages, as in k_recover_tc)
             if (epi_sync_or(!got)) break;
-            epi_store(a, a.work[bt], et, os, t);
+            epi_store(a, er, rowoff[er.buf], et, os, t);
         }
     }
     __syncthreads();
@@ -653,6 +726,9 @@ void recover_vm_tcs(mstress_sol_s* s, float* out) {
     ra.err = s->flag.as<int>() + 2;
     const long long pairs = (long long)s->n_awork_rec * sh.n_etiles;
     const int grid = (int)std::max(1LL, std::min(pairs, (long long)ctx->num_sms));
+    // about eight units per CTA at least, so that the last round is nearly full
+    ra.n_seg = (int)std::max(1LL, std::min((long long)sh.n_etiles,
+                                           (8LL * grid + s->n_awork_rec - 1) / std::max(1, s->n_awork_rec)));
     switch (prec) {
         case MSTRESS_TF32: k_recover_tcs<MSTRESS_TF32><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
         case MSTRESS_BF16: k_recover_tcs<MSTRESS_BF16><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
