@@ -33,10 +33,11 @@ METRIC = "TSV blocks solved+recovered/s (100x100 array)"
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
 DTYPE = {"fp64": "f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64", "bf16x3": "bf16x3+f32+f64"}
 ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch divided by
-# the launch's PCG iterations, per precision (profiles/k_pcg_array100.md);
-# absent until taken for the current kernel.
-PCG_TRAFFIC = {}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_pcg launches of one
+# 100x100 solve divided by its PCG iterations, per precision (bytes per
+# iteration; profiles/launches_array100.md: 30.74 MB over 341 iterations);
+# absent for a precision not measured with the current kernel.
+PCG_TRAFFIC = {"bf16x3": 90150}
 
 
 def parse():
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--nx", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="array100", choices=["array100", "batch256", "serve"],
@@ -314,8 +315,9 @@ def ours(args):
                 "kernel": "k_pcg (persistent PCG: tensor-core apply + interface sum + vector update)",
                 "peak_source": hbm_src,
                 "note": "vectors are L2-resident at this size, so the iteration is latency-bound (three grid "
-                        "barriers and folds per iteration), not HBM-bound; traffic = ncu dram bytes of one "
-                        "k_pcg launch divided by its iterations (profiles/)"}
+                        "barriers and folds per iteration), not HBM-bound; traffic = ncu dram bytes of the "
+                        "k_pcg launches of one solve divided by its iterations, bytes per iteration "
+                        "(profiles/launches_array100.md)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["algorithmic_bytes_per_iteration"] = it_bytes
     roof["per_iteration_ms"] = {"apply": t_apply, "isum": ph["isum"] / n_iter, "update": ph["update"] / n_iter}
