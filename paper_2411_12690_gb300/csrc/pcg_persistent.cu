@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     __shared__ unsigned s_kbar;   // grid barriers passed by this CTA
     __shared__ double s_scalar;
     __shared__ ArrayDev s_A;
+    // one array: every CTA keeps the scalars itself (see below)
+    __shared__ double s_rz, s_beta, s_alpha, s_tol2;
+    __shared__ int s_iters, s_max_iter;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ __align__(8) uint64_t bars[3 * 4 + 2];
     __shared__ int s_tcs_fail;
@@ -226,7 +229,31 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         }
     };
 
-    if (tid == 0) s_kbar = 0;   // read first by thread 0 itself in the first barrier
+    // One array (a single solve): after each reducing phase's grid barrier every
+    // CTA folds all partial sums itself, in the same fixed order as the
+    // ticket path, and keeps alpha, beta, rz and the stopping decision in
+    // shared memory. The scalars are bitwise those of the ticket path (so a
+    // solve alone and in a batch still agree) without the ticket atomic, the
+    // fold by the last CTA and the broadcast through global memory on the
+    // critical path. Every CTA stores the same beta for its own next gather;
+    // CTA 0 writes the rest of the state for the host. (Not compiled for the
+    // streamed tensor-core apply, whose registers are fully used and whose
+    // workloads are batches.)
+    const bool solo = AM != AM_TCS && a.n_arrays == 1;
+    if (tid == 0) {
+        s_kbar = 0;   // read first by thread 0 itself in the first barrier
+        if (solo) {
+            s_A = a.arrays[0];
+            s_rz = __ldcg(&a.st[0].rz);
+            s_beta = __ldcg(&a.st[0].beta);
+            s_tol2 = __ldcg(&a.st[0].tol2);
+            s_iters = __ldcg(&a.st[0].iters);
+            s_max_iter = __ldcg(&a.st[0].max_iter);
+            s_active = __ldcg(&a.st[0].active);
+            s_scalar = s_beta;
+        }
+    }
+    __syncthreads();
     unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
@@ -264,7 +291,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         phase_mark(a, 0, t_prev);
         // ---- phase B: interface sum, <p, q>, alpha
         {
-            ArrayCursor cur{-1, 0};
+            // one array: the cursor starts on it (s_A, s_active, s_scalar = beta preset)
+            ArrayCursor cur{solo ? 0 : -1, 0};
             VecWork next = blockIdx.x < a.n_vwork ? a.vwork[blockIdx.x] : VecWork{};
             for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
                 const VecWork it = next;
@@ -277,13 +305,34 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 if (tid == 0) a.part_pq[w] = t;
                 cur.count += 1;
             }
-            switch_array(cur, -1, 1);
+            if (!solo) switch_array(cur, -1, 1);
         }
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 1, t_prev);
+        if (solo && s_active) {
+            const double pq = pi::cta_fold8(a.part_pq + s_A.vwork_off, s_A.n_vwork, sh8);
+            if (tid == 0) {
+                const double al = s_rz / pq;
+                if (!(pq > 0) || !isfinite(al)) {
+                    s_alpha = 0.0;
+                    s_active = 0;
+                    if (blockIdx.x == 0) {
+                        a.st[0].alpha = 0.0;
+                        a.st[0].active = 0;
+                        a.st[0].status = MSTRESS_ENUMERIC;
+                        atomicSub(a.n_active, 1);
+                    }
+                } else {
+                    s_alpha = al;
+                    if (blockIdx.x == 0) a.st[0].alpha = al;
+                }
+                s_scalar = s_alpha;
+            }
+            __syncthreads();
+        }
         // ---- phase C: vector update, <r,z>, <r,r>, beta, stopping test
         {
-            ArrayCursor cur{-1, 0};
+            ArrayCursor cur{solo ? 0 : -1, 0};   // one array: s_scalar = alpha preset
             VecWork next = blockIdx.x < a.n_vwork ? a.vwork[blockIdx.x] : VecWork{};
             for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
                 const VecWork it = next;
@@ -300,12 +349,44 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 }
                 cur.count += 1;
             }
-            switch_array(cur, -1, 2);
+            if (!solo) switch_array(cur, -1, 2);
         }
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 2, t_prev);
+        if (solo && s_active) {
+            double rz, rr;
+            pi::cta_fold8_2(a.part_rz + s_A.vwork_off, a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8, rz, rr);
+            if (tid == 0) {
+                const int iters = s_iters + 1;
+                int active = 1, status = MSTRESS_OK;
+                double beta = 0;
+                if (!isfinite(rz) || !isfinite(rr)) {
+                    active = 0;
+                    status = MSTRESS_ENUMERIC;
+                } else {
+                    beta = rz / s_rz;
+                    if (rr <= s_tol2) active = 0;
+                    else if (iters >= s_max_iter) { active = 0; status = MSTRESS_ENOT_CONVERGED; }
+                }
+                s_rz = rz;
+                s_beta = beta;
+                s_scalar = beta;
+                s_iters = iters;
+                s_active = active;
+                a.st[0].beta = beta;   // the same value from every CTA, read by its own next gather
+                if (blockIdx.x == 0) {
+                    a.st[0].rz = rz;
+                    a.st[0].rr = rr;
+                    a.st[0].iters = iters;
+                    a.st[0].status = status;
+                    a.st[0].active = active;
+                    if (!active) atomicSub(a.n_active, 1);
+                }
+            }
+            __syncthreads();
+        }
         if (a.timers && blockIdx.x == 0 && tid == 0) a.timers[3] += 1;
-        if (*(volatile int*)a.n_active <= 0) break;
+        if (solo ? !s_active : *(volatile int*)a.n_active <= 0) break;
     }
     if constexpr (AM == AM_TC) {
         if (*(volatile int*)a.abort) tc::mbar_wait(&mbar, ts.phase ^ 1u, 1 << 20);   // bounded drain
