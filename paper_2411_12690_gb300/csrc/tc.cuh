@@ -3,12 +3,14 @@
 // instruction descriptors, MMA issue/commit, mbarrier waits with an iteration
 // limit, and tensor-memory loads.
 //
-// Operand layout used everywhere here: K-major, no swizzle. The smallest unit
-// is a "core matrix" of 8 rows x 16 bytes stored as 128 contiguous bytes (row
-// r at byte 16 r). Core matrices adjacent along K are LBO = 128 bytes apart;
-// groups of 8 rows are SBO = (K bytes / 16) * 128 bytes apart. One MMA
-// consumes 32 bytes of K (two core matrices), so consecutive K steps advance
-// the descriptor start address by 256 bytes.
+// Operand layouts, both K-major. (1) No swizzle, for the apply and the
+// recovery of small bases: the smallest unit is a "core matrix" of 8 rows x 16
+// bytes stored as 128 contiguous bytes (row r at byte 16 r). Core matrices
+// adjacent along K are LBO = 128 bytes apart; groups of 8 rows are SBO =
+// (K bytes / 16) * 128 bytes apart. One MMA consumes 32 bytes of K (two core
+// matrices), so consecutive K steps advance the descriptor start address by
+// 256 bytes. (2) 128-byte swizzle, for the streamed recovery of large bases
+// (described at sw128_offset below).
 #pragma once
 
 #include <cstdint>
