@@ -101,6 +101,20 @@ def cpu_baseline_entry(res: dict) -> dict:
                       f"direct solve grows faster than linearly, so this overstates the oracle at 100x100"}
 
 
+def whole_job_rate(dist, world: int, units_per_rank: float, rank_seconds: float, device="cuda"):
+    """Whole-job throughput of `world` replicas: every rank's units over the
+    slowest rank's time (barrier, then the max of the ranks' times). Returns
+    (units per second, slowest rank's seconds). dist is torch.distributed or
+    None for a single process."""
+    import torch
+    t = torch.tensor([rank_seconds], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return world * units_per_rank / slowest, slowest
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -240,12 +254,8 @@ def ours(args):
         sol.close()
     launches = api.launch_count() - l0
     clk = clocks.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * n_blocks * args.steps / (total_ms / 1e3)
+    value, slowest = whole_job_rate(dist, world, n_blocks * args.steps, total_ms / 1e3)
+    total_ms = 1e3 * slowest
 
     # end to end: host inputs (site map, dT) in, von Mises to pinned host memory, every step
     e2e_t = 0.0
@@ -257,10 +267,7 @@ def ours(args):
         s2.recover(L.MSTRESS_VM_ELEM, out=vm_host)
         e2e_t += time.perf_counter() - t0
         s2.close()
-    et = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_value = world * n_blocks * args.steps / float(et.item())
+    e2e_value, _ = whole_job_rate(dist, world, n_blocks * args.steps, e2e_t)
 
     # roofline of the dominant kernel. The PCG runs as one persistent kernel
     # (k_pcg) whose phases are timed on the device (globaltimer at its grid
