@@ -121,7 +121,9 @@ typedef struct {
     int precision;        /* MSTRESS_FP64 | _TF32 | _BF16 | _BF16X3           */
     double rtol;          /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64)   */
     int max_iter;         /* PCG iteration limit (inner iterations summed)     */
-    double inner_rtol;    /* mixed modes: inner PCG relative tolerance         */
+    double inner_rtol;    /* mixed modes: inner PCG relative tolerance (an inner
+                             solve also stops below a tenth of the outer
+                             tolerance)                                     */
     int max_outer;        /* mixed modes: refinement step limit                */
     size_t hbm_budget;    /* bytes this context may hold on the device; 0 = all */
     int offline_max_iter; /* local-stage CG iteration limit                    */

@@ -352,7 +352,12 @@ __global__ void __launch_bounds__(1024) k_scalars(const __grid_constant__ Scalar
                 s.rz = rz;
                 s.rr = rr;
                 s.bb = rr;
+                // the inner solve of a refinement step (gate = outer state) also
+                // stops once its residual is below a tenth of the outer
+                // tolerance: the last step needs only the reduction that is
+                // left, and the outer FP64 residual decides convergence
                 s.tol2 = a.rtol * a.rtol * rr;
+                if (a.gate) s.tol2 = fmax(s.tol2, 0.01 * a.gate[k].tol2);
                 s.beta = 0.0;
                 s.iters = 0;
                 s.max_iter = a.max_iter;
