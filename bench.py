@@ -35,9 +35,11 @@ DTYPE = {"fp64": "f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64", "bf16x3"
 ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_pcg launches of one
 # 100x100 solve divided by its PCG iterations, per precision (bytes per
-# iteration; profiles/launches_array100.md: 30.85 MB over 341 iterations);
-# absent for a precision not measured with the current kernel.
-PCG_TRAFFIC = {"bf16x3": 90460}
+# iteration; profiles/launches_array100.md: 30.85 MB over the 4 launches of a
+# solve, nearly the same for every launch whatever its length, over the
+# solve's 315 iterations); absent for a precision not measured with the
+# current kernel.
+PCG_TRAFFIC = {"bf16x3": 97940}
 
 
 def parse():
