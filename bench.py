@@ -35,10 +35,9 @@ DTYPE = {"fp64": "f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64", "bf16x3"
 ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_pcg launches of one
 # 100x100 solve divided by its PCG iterations, per precision (bytes per
-# iteration; profiles/launches_array100.md: 30.85 MB over the 4 launches of a
-# solve, nearly the same for every launch whatever its length, over the
-# solve's 315 iterations); absent for a precision not measured with the
-# current kernel.
+# iteration: 30.85 MB over the 4 launches of a solve, nearly the same for every
+# launch whatever its length, over the solve's 315 iterations); absent for a
+# precision not measured with the current kernel.
 PCG_TRAFFIC = {"bf16x3": 97940}
 
 
@@ -325,8 +324,7 @@ def ours(args):
                 "peak_source": hbm_src,
                 "note": "vectors are L2-resident at this size, so the iteration is latency-bound (three grid "
                         "barriers and folds per iteration), not HBM-bound; traffic = ncu dram bytes of the "
-                        "k_pcg launches of one solve divided by its iterations, bytes per iteration "
-                        "(profiles/launches_array100.md)"}
+                        "k_pcg launches of one solve divided by its iterations, bytes per iteration"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["algorithmic_bytes_per_iteration"] = it_bytes
     roof["per_iteration_ms"] = {"apply": t_apply, "isum": ph["isum"] / n_iter, "update": ph["update"] / n_iter}

@@ -181,6 +181,9 @@ int mstress_block_import(mstress_ctx ctx, const mstress_block_mesh* mesh, int or
 int mstress_block_export(mstress_block blk, int what, double* dst, size_t count);
 /* m (element DOFs), n_el (fine elements), n_dof (fine DOFs), cg_iters (local stage). */
 int mstress_block_info(mstress_block blk, int* m, int* n_el, int* n_dof, int* cg_iters);
+/* Free a block model. Work the library issued on the context's stream is
+   waited for; work that mstress_apply_noalloc issued on another stream with
+   this block is not, so the caller must finish it first. */
 void mstress_free_block(mstress_block blk);
 
 /* ------------------------------------------------------- global stage
@@ -227,6 +230,13 @@ int mstress_recover(mstress_ctx ctx, mstress_sol sol, int what, void* dst,
 int mstress_sol_info(mstress_sol sol, int array, int* iters, int* outer,
                      double* rel_res, int* status);
 int mstress_sol_count(mstress_sol sol, int* n_arrays, int64_t* n_blocks);
+/* How the solve's reduced-precision operator ran: *use_tc = 1 if on the
+   tensor cores, *tc_tile = blocks per tensor-core tile (the M extent filled
+   per MMA tile; 0 when the tensor cores are not used), *tuned = 1 if the tile
+   autotuner picked it (solves of at least two blocks per SM; the choice is
+   timed once per basis size, precision and batch-size class and then reused
+   by the context). Any pointer may be NULL. */
+int mstress_sol_tiling(mstress_sol sol, int* use_tc, int* tc_tile, int* tuned);
 void mstress_free_sol(mstress_sol sol);
 
 /* ------------------------------------------------------------ serving
@@ -313,11 +323,15 @@ int mstress_apply(mstress_ctx ctx, const mstress_layout* layout, const double* x
    32 MiB device array inside the library that every GPU loading the library
    holds until the process exits: nx*ny*round_up(m,16)*8 bytes must fit (e.g.
    at most 52428 blocks at m = 78, 13797 at m = 294), else MSTRESS_EINVAL.
-   The first call on a device looks up that array's address (and must come
-   before any stream capture); later calls make no set-up call. Every call
-   shares the array and leaves its contents behind (nothing in it needs to
-   start at zero); calls whose work may overlap on the GPU race on it and must
-   be serialised by the caller. */
+   The first call on a device looks up that array's address; it must come
+   before any stream capture, and on a stream that is being captured it is
+   refused with MSTRESS_EINVAL. Later calls make no set-up call. The device
+   of blk's context must be the current device (else MSTRESS_EINVAL). Every
+   call shares the array and leaves its contents behind (nothing in it needs
+   to start at zero); calls whose work may overlap on the GPU race on it and
+   must be serialised by the caller. The call reads blk's K_r on cuda_stream
+   without recording that use: the caller must let that work finish (e.g.
+   cudaStreamSynchronize(cuda_stream)) before mstress_free_block(blk). */
 int mstress_apply_noalloc(mstress_block blk, int nx, int ny, const double* x_dev, double* y_dev,
                           void* cuda_stream);
 

@@ -104,6 +104,7 @@ SIGNATURES = {
     "mstress_recover": (I, [P, P, I, P, C.c_size_t, I]),
     "mstress_sol_info": (I, [P, I, PI, PI, PD, PI]),
     "mstress_sol_count": (I, [P, PI, C.POINTER(C.c_int64)]),
+    "mstress_sol_tiling": (I, [P, PI, PI, PI]),
     "mstress_free_sol": (None, [P]),
     "mstress_apply": (I, [P, C.POINTER(mstress_layout), P, P, I]),
     "mstress_launch_count": (I, [C.POINTER(C.c_int64)]),

@@ -232,6 +232,14 @@ class Solution:
                                                       C.byref(st)))
         return dict(iters=it.value, outer=outer.value, rel_res=rr.value, status=st.value)
 
+    def tiling(self):
+        """Whether the reduced-precision operator ran on the tensor cores, the
+        blocks per tensor-core tile the solve used, and whether the autotuner
+        picked that tile."""
+        u, t, a = C.c_int(), C.c_int(), C.c_int()
+        self.ctx._check(self.ctx.lib.mstress_sol_tiling(self.h, C.byref(u), C.byref(t), C.byref(a)))
+        return dict(use_tc=bool(u.value), tc_tile=t.value, tuned=bool(a.value))
+
     def phase_ms(self):
         """Device time in the persistent solver's phases (element products,
         interface sum, vector update), summed over iterations, and the count."""

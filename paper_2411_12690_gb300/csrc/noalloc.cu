@@ -14,8 +14,10 @@
 //
 // Set-up: the device address of the scratch array is looked up with
 // cudaGetSymbolAddress the first time the entry point runs on a device (with
-// that device current) and cached; make that first call before any stream
-// capture. Every call shares the one array, which keeps the last call's
+// that device current) and cached; that first call must come before any
+// stream capture and is refused (MSTRESS_EINVAL) on a capturing stream. The
+// block's context device must be the current device. The block must outlive
+// the work issued on cuda_stream: free it only after that work has finished. Every call shares the one array, which keeps the last call's
 // contents; nothing in it needs to start at zero because each call writes
 // every entry it reads. Calls whose work overlaps on the GPU (different
 // streams, or different host threads on one stream without ordering) race on
@@ -91,14 +93,19 @@ __global__ void __launch_bounds__(kNaThreads) k_na_isum(const __grid_constant__ 
 std::mutex g_scratch_mutex;
 void* g_scratch_ptr[64] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (together with the apply kernel's shared-memory limit).
-double* scratch_for_current_device() {
-    int dev = 0;
-    MS_CUDA(cudaGetDevice(&dev));
+// Device address of the scratch array on device dev (which must be current),
+// looked up once per device (together with the apply kernel's shared-memory
+// limit). The look-up is refused while `st` is being captured into a graph:
+// the set-up calls would invalidate the caller's capture.
+double* scratch_for_device(int dev, cudaStream_t st) {
     MS_REQUIRE(dev >= 0 && dev < 64, MSTRESS_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_ptr[dev]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        MS_CUDA(cudaStreamIsCapturing(st, &cs));
+        MS_REQUIRE(cs == cudaStreamCaptureStatusNone, MSTRESS_EINVAL,
+                   "the first mstress_apply_noalloc call on a device sets up its scratch and must not be "
+                   "captured: make one call before the capture begins");
         void* p = nullptr;
         MS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         MS_CUDA(cudaFuncSetAttribute(k_na_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -120,6 +127,11 @@ extern "C" int mstress_apply_noalloc(mstress_block blk, int nx, int ny, const do
     try {
         MS_REQUIRE(x_dev && y_dev, MSTRESS_EINVAL, "x and y are required");
         MS_REQUIRE(nx >= 1 && ny >= 1, MSTRESS_EINVAL, "array needs nx, ny >= 1");
+        int dev = -1;
+        MS_CUDA(cudaGetDevice(&dev));
+        MS_REQUIRE(dev == ctx->device, MSTRESS_EINVAL,
+                   "the block's device (" + std::to_string(ctx->device) + ") is not the current device (" +
+                       std::to_string(dev) + ")");
         NaArgs a;
         std::memset(&a, 0, sizeof(a));
         a.lm = make_local_map(blk->n);
@@ -141,8 +153,8 @@ extern "C" int mstress_apply_noalloc(mstress_block blk, int nx, int ny, const do
         a.K = blk->Kr.as<double>();
         a.x = x_dev;
         a.y = y_dev;
-        a.Y = scratch_for_current_device();
         cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        a.Y = scratch_for_device(dev, st);
         const size_t smem = (size_t)a.m * kNaTile * sizeof(double);
         k_na_apply<<<(unsigned)((n_blocks + kNaTile - 1) / kNaTile), kNaThreads, smem, st>>>(a);
         MS_LAUNCH_CHECK();

@@ -907,6 +907,7 @@ void autotune_tc_tile(mstress_sol_s* s) {
     const int cls = 64 - __builtin_clzll((unsigned long long)s->n_blocks);
     const uint64_t key = ((uint64_t)s->m << 40) | ((uint64_t)s->precision << 32) | (uint64_t)cls;
     auto hit = ctx->tile_choice.find(key);
+    s->tuned = true;
     if (hit != ctx->tile_choice.end()) {
         if (hit->second != s->tc_tile) set_tc_tiles(s, hit->second);
         return;
@@ -928,6 +929,7 @@ void autotune_tc_tile(mstress_sol_s* s) {
         if (!pcg_run_persistent(s, s->v32, s->precision, kTrialIters, true)) {
             best_ns = -1;   // no cooperative launch: keep the default tiles
             best = h;
+            s->tuned = false;
             break;
         }
         unsigned long long t[4];
@@ -1149,6 +1151,14 @@ int mstress_sol_info(mstress_sol sol, int array, int* iters, int* outer, double*
     if (outer) *outer = r.outer;
     if (rel_res) *rel_res = r.rel_res;
     if (status) *status = r.status;
+    return MSTRESS_OK;
+}
+
+int mstress_sol_tiling(mstress_sol sol, int* use_tc, int* tc_tile, int* tuned) {
+    if (!sol) return MSTRESS_EINVAL;
+    if (use_tc) *use_tc = sol->use_tc ? 1 : 0;
+    if (tc_tile) *tc_tile = sol->use_tc ? sol->tc_tile : 0;
+    if (tuned) *tuned = sol->tuned ? 1 : 0;
     return MSTRESS_OK;
 }
 

@@ -91,6 +91,7 @@ struct mstress_sol_s {
     int n_awork = 0, n_awork_tc = 0, n_awork_rec = 0, n_vwork = 0;
     std::vector<ms::ApplyWork> h_awork, h_awork_rec;   // host copies (filtered recovery)
     std::vector<ms::ApplyWork> h_seg;     // (type, array) runs of the block list (count = run length)
+    bool tuned = false;                   // tc_tile picked (or recalled) by the tile autotuner
     int tc_tile = 128;                    // blocks per tensor-core apply tile (<= 128, a multiple of 8: about
                                           // one tile per SM when the batch is small; smaller tiles
                                           // spread a small array's gather over more SMs)

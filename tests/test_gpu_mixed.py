@@ -14,30 +14,19 @@ Stated accuracy, per output:
 import numpy as np
 import pytest
 
-from cases import oracle_pair, oracle_solve, rel_l2
+from cases import oracle_pair, oracle_solve, rel_l2, vm_bound_rows
 from oracle import fem, mor
 from paper_2411_12690_gb300 import _lib as L
 from paper_2411_12690_gb300 import workloads as W
 
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
 
-U_IN = {L.MSTRESS_TF32: 2.0 ** -11, L.MSTRESS_BF16: 2.0 ** -8, L.MSTRESS_BF16X3: 3 * 2.0 ** -16}
 MODES = [L.MSTRESS_TF32, L.MSTRESS_BF16, L.MSTRESS_BF16X3]
 
 
 def vm_bound(blocks, osol, mode):
     """Per-element bound on |vm_gpu - vm_exact| from the recovery rounding."""
-    m1 = blocks[0].m + 1
-    u = 2 * U_IN[mode] + (m1 + 16) * 2.0 ** -24     # + FP32 rounding of the von Mises epilogue
-    out = []
-    for k, t in enumerate(osol.site_type.ravel()):
-        b = blocks[int(t)]
-        Sm = np.abs(b.S.reshape(b.n_el, 8, 6, m1).mean(axis=1))          # (n_el, 6, m1)
-        cc = np.abs(np.concatenate([osol.coeffs[k], [osol.dT]]))
-        ab = u * (Sm @ cc)                                               # (n_el, 6)
-        fro = np.sqrt((ab[:, :3] ** 2).sum(1) + 2 * (ab[:, 3:] ** 2).sum(1))
-        out.append(np.sqrt(1.5) * fro)
-    return np.stack(out)
+    return vm_bound_rows(blocks, osol.site_type.ravel(), osol.coeffs, osol.dT, mode)
 
 
 @pytest.fixture(scope="module")

@@ -151,3 +151,62 @@ def test_lame_cylinder_closed_form():
     assert e[0] > e[1] > e[2]
     assert e[2] < 0.05
     assert errs[2][1] < 0.02      # sigma_zz = -E alpha dT in the matrix (plane strain)
+
+
+# ------------------------------------------- voxelised TSV block: census
+# Hand-derived element census of the voxeliser (section 4.2, Fig. 2: Cu core of
+# radius d/2 = 2.5 um, SiO2 liner of t = 0.5 um outside it, Si elsewhere; an
+# element takes the material at its centroid). In a block of side p meshed by
+# c x c cells (h = p / c, c even), the centroids of one quarter of a layer sit
+# at offsets (a h, b h) from the axis with a, b in {1/2, 3/2, ...}. So an
+# element is Cu iff a^2 + b^2 <= (2.5 / h)^2 and SiO2 iff it is not Cu and
+# a^2 + b^2 <= (3.0 / h)^2; no centroid lies on either circle for these sizes
+# (a^2 + b^2 = (odd^2 + odd^2) / 4 is never 9, 12.96, 16 or 23.04).
+#   p = 10, c = 12 (h = 5/6): (2.5/h)^2 = 9, (3/h)^2 = 12.96.
+#     Cu per quarter: (1/2,1/2) (1/2,3/2)x2 (1/2,5/2)x2 (3/2,3/2) (3/2,5/2)x2 = 8;
+#     SiO2 per quarter: (5/2,5/2) [12.5] and (1/2,7/2)x2 [12.5] = 3;
+#     per layer Cu 32, SiO2 12, Si 144 - 44 = 100.
+#   p = 15, c = 24 (h = 5/8): (2.5/h)^2 = 16, (3/h)^2 = 23.04.
+#     b-counts per a = 1/2, 3/2, 5/2, 7/2: Cu 4 + 4 + 3 + 2 = 13 per quarter;
+#     within 23.04 per a = 1/2 .. 9/2: 5 + 5 + 4 + 3 + 2 = 19, so SiO2 6 per
+#     quarter; per layer Cu 52, SiO2 24, Si 576 - 76 = 500.
+#   p = 20, c = 24 (h = 5/6): the same radii in cells as p = 10, c = 12, so Cu
+#     32, SiO2 12 and Si 576 - 44 = 532 per layer.
+CENSUS = [  # (lx, cells, ez, Cu, SiO2, Si per layer)
+    (10.0, 12, 10, 32, 12, 100),
+    (15.0, 24, 20, 52, 24, 500),
+    (20.0, 24, 20, 32, 12, 532),
+]
+
+
+@pytest.mark.parametrize("lx,c,ez,n_cu,n_ox,n_si", CENSUS)
+def test_voxelised_tsv_census(lx, c, ez, n_cu, n_ox, n_si):
+    ids = fem.tsv_material_ids(lx, lx, 50.0, c, c, ez, 2.5, 0.5).reshape(ez, c, c)   # [kz, ky, kx]
+    for kz in range(ez):   # every layer identical (a straight through-via)
+        assert np.array_equal(ids[kz], ids[0])
+    cnt = np.bincount(ids[0].ravel(), minlength=3)
+    assert tuple(cnt) == (n_si, n_cu, n_ox)
+    # the axis is the block centre: the layer map has the square's eight symmetries
+    lay = ids[0]
+    for t in (lay[::-1, :], lay[:, ::-1], lay.T):
+        assert np.array_equal(t, lay)
+    # Cu at the four cells around the axis; Si in the corners
+    h = c // 2
+    assert np.all(lay[h - 1:h + 1, h - 1:h + 1] == 1)
+    assert lay[0, 0] == lay[-1, -1] == 0
+    # dummy block: all Si
+    assert np.all(fem.tsv_material_ids(lx, lx, 50.0, c, c, ez, 0.0, 0.0) == 0)
+
+
+def test_voxelised_liner_cells_p10():
+    """The SiO2 cells of the p = 10 um, 12-cell block are exactly those with
+    centroid offsets (5/2, 5/2) h (r = 2.946 um) and (1/2, 7/2) h, (7/2, 1/2) h
+    (r = 2.946 um) in each quarter: the liner sits outside the Cu radius."""
+    lay = fem.tsv_material_ids(10.0, 10.0, 50.0, 12, 12, 10, 2.5, 0.5).reshape(10, 12, 12)[0]
+    want = set()
+    for a, b in ((2.5, 2.5), (0.5, 3.5), (3.5, 0.5)):
+        for sa in (-1, 1):
+            for sb in (-1, 1):
+                want.add((int(5.5 + sb * b + 0.5), int(5.5 + sa * a + 0.5)))   # (ky, kx)
+    got = {(int(ky), int(kx)) for ky, kx in zip(*np.nonzero(lay == 2))}
+    assert got == want

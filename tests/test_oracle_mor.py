@@ -211,3 +211,77 @@ def test_clamped_face_is_clamped_in_the_fine_field(small_block):
     for k in range(2):
         u = mor.block_displacement(small_block, sol.coeffs[k], -250.0).reshape(-1, 3)
         assert np.abs(u[bottom]).max() == 0.0
+
+
+def _mirror_checks(u3, tol):
+    """u3[z, y, x, comp] on a grid symmetric about its mid-planes, of a
+    homogeneous body under a uniform dT with both z faces clamped: reflection
+    about z = h/2 keeps u_x, u_y and flips u_z; reflection about x = L/2 flips
+    u_x and keeps u_y, u_z (and likewise in y)."""
+    zr = u3[::-1]
+    assert np.abs(zr[..., :2] - u3[..., :2]).max() <= tol
+    assert np.abs(zr[..., 2] + u3[..., 2]).max() <= tol
+    xr = u3[:, :, ::-1]
+    assert np.abs(xr[..., 0] + u3[..., 0]).max() <= tol
+    assert np.abs(xr[..., 1:] - u3[..., 1:]).max() <= tol
+    yr = u3[:, ::-1]
+    assert np.abs(yr[..., 1] + u3[..., 1]).max() <= tol
+    assert np.abs(yr[..., [0, 2]] - u3[..., [0, 2]]).max() <= tol
+
+
+def test_top_and_bottom_clamp_symmetry():
+    """Scenario 1 of section 5.2 clamps the top and the bottom face. For a
+    homogeneous (pure-Si) array under uniform dT the clamped slab is symmetric
+    about its mid-plane: both z faces stay fixed, u_z vanishes on the
+    mid-plane, u_x, u_y are even and u_z odd in z - h/2 (O-FEM and O-MOR);
+    with the bottom clamp alone the free top face rises and the symmetry is
+    lost. Clamping the wrong layer, or not clamping the top, breaks these."""
+    dT = -250.0
+    ex, ey, ez = 4, 4, 6
+    dum = fem.tsv_block_mesh(10.0, 10.0, 20.0, ex, ey, ez, 0.0, 0.0)
+    st = np.zeros((2, 3), dtype=int)
+    amesh, u, _ = fem.solve_array_fem(dum, [dum.mat_id], st, dT, clamp_bottom=True, clamp_top=True)
+    u3 = u.reshape(ez + 1, 2 * ey + 1, 3 * ex + 1, 3)
+    scale = np.abs(u3).max()
+    assert scale > 0
+    assert np.abs(u3[0]).max() == 0.0 and np.abs(u3[-1]).max() == 0.0
+    assert np.abs(u3[ez // 2, :, :, 2]).max() <= 1e-12 * scale
+    _mirror_checks(u3, 1e-11 * scale)
+    _, ub, _ = fem.solve_array_fem(dum, [dum.mat_id], st, dT, clamp_bottom=True, clamp_top=False)
+    assert np.abs(ub.reshape(u3.shape)[-1, :, :, 2]).max() > 0.1 * scale   # free top face moves
+
+    blk = mor.local_stage(dum, (3, 3, 3))
+    sol = mor.global_stage([blk], st, dT, clamp_bottom=True, clamp_top=True)
+    X, Y, Z = sol.lattice_shape
+    lat = np.zeros((Z, Y, X, 3))
+    idx = sol.lattice_of_dof.reshape(-1, 3)[:, 0]
+    lat.reshape(-1, 3)[idx] = sol.u.reshape(-1, 3)
+    s2 = np.abs(lat).max()
+    assert s2 > 0
+    assert np.abs(lat[0]).max() == 0.0 and np.abs(lat[-1]).max() == 0.0
+    assert np.abs(lat[Z // 2, :, :, 2]).max() <= 1e-12 * s2
+    _mirror_checks(lat, 1e-11 * s2)
+    fixed = sol.fixed.reshape(-1, 3)
+    gz = idx // (X * Y)
+    assert np.array_equal(fixed.all(axis=1), (gz == 0) | (gz == Z - 1))
+
+
+def test_exact_static_condensation_top_clamped():
+    """The exact static-condensation pin (every fine boundary node a Lagrange
+    node) with the top face clamped as well: O-MOR's clamp of the top lattice
+    layer equals O-FEM's clamp of the top mesh face."""
+    ex, ey, ez = 4, 4, 3
+    tsv = fem.tsv_block_mesh(10.0, 10.0, 20.0, ex, ey, ez, 2.5, 0.5)
+    dum = fem.tsv_block_mesh(10.0, 10.0, 20.0, ex, ey, ez, 0.0, 0.0)
+    nxyz = (ex + 1, ey + 1, ez + 1)
+    blocks = [mor.local_stage(tsv, nxyz), mor.local_stage(dum, nxyz)]
+    st = np.array([[0, 1, 0]])
+    dT = -250.0
+    sol = mor.global_stage(blocks, st, dT, clamp_bottom=True, clamp_top=True)
+    amesh, u_fem, _ = fem.solve_array_fem(tsv, _site_mats(tsv, dum), st, dT, clamp_bottom=True, clamp_top=True)
+    nid = amesh.node_index()
+    for i in range(3):
+        blk = blocks[st[0, i]]
+        ub = mor.block_displacement(blk, sol.coeffs[i], dT).reshape(-1, 3)
+        ids = nid[i * ex:(i + 1) * ex + 1, 0:ey + 1, :].transpose(2, 1, 0).ravel()
+        assert np.abs(ub - u_fem.reshape(-1, 3)[ids]).max() <= 1e-10 * np.abs(u_fem).max()
