@@ -161,6 +161,8 @@ struct TcShape {
     int lg_tile;                 // log2 of the blocks per tile of the solve (rows gathered per tile)
     uint32_t a_plane, b_plane;   // bytes per operand plane (multiples of 1024)
     size_t smem;                 // dynamic shared memory of a CTA using this shape
+    int ldp;                     // row stride (floats) of the FP32 copy of the gathered tile
+    size_t dot_smem;             // extra shared memory for the epilogue dot products (FP32 tile + chunk sums)
 };
 
 }  // namespace ai
@@ -220,11 +222,15 @@ __device__ __forceinline__ void operand_load(const float* __restrict__ x, const 
 
 template <int MODE, int GU>
 __device__ __forceinline__ void operand_store(int lg_tile, int total, int idx0, const float (&v)[GU], uint8_t* plane0,
-                                              uint32_t plane_bytes, uint32_t sbo) {
+                                              uint32_t plane_bytes, uint32_t sbo, float* sP = nullptr, int ldp = 0,
+                                              int kg0 = 0) {
 #pragma unroll
     for (int u = 0; u < GU; ++u) {
         const int idx = idx0 + u * (int)blockDim.x;
-        if (idx < total) put_operand(plane0, plane_bytes, OperandMap<MODE>::off(idx, lg_tile, sbo), v[u], MODE);
+        if (idx < total) {
+            put_operand(plane0, plane_bytes, OperandMap<MODE>::off(idx, lg_tile, sbo), v[u], MODE);
+            if (sP) sP[OperandMap<MODE>::row(idx, lg_tile) * ldp + OperandMap<MODE>::col(idx, lg_tile, kg0)] = v[u];
+        }
     }
 }
 
@@ -236,16 +242,19 @@ __device__ __forceinline__ void operand_store(int lg_tile, int total, int idx0, 
 // contiguous shared memory (no bank conflicts) and its loads run along a
 // block's contiguous lattice DOFs. Rows [count, 1 << lg_tile) and columns
 // >= m are written as zeros. Eight values per thread are in flight at a time.
+// With sP, the gathered FP32 values are also kept at sP[row * ldp + column]
+// (the element DOFs p_e for the dot products p_e^T Y_e of the epilogue).
 template <int MODE>
 __device__ __forceinline__ void gather_operand(const float* __restrict__ x, const float* __restrict__ z, float beta,
                                                int m, int count, const long long* base, const int* offs, int lg_tile,
-                                               int kg0, int nkg, uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo) {
+                                               int kg0, int nkg, uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo,
+                                               float* sP = nullptr, int ldp = 0) {
     constexpr int GU = 8;
     const int total = nkg << (lg_tile + OperandMap<MODE>::LGKE);
     for (int idx0 = threadIdx.x; idx0 < total; idx0 += (int)blockDim.x * GU) {
         float v[GU];
         operand_load<MODE, GU>(x, z, beta, m, count, base, offs, lg_tile, kg0, total, idx0, v);
-        operand_store<MODE, GU>(lg_tile, total, idx0, v, plane0, plane_bytes, sbo);
+        operand_store<MODE, GU>(lg_tile, total, idx0, v, plane0, plane_bytes, sbo, sP, ldp, kg0);
     }
 }
 
@@ -257,6 +266,9 @@ struct TcState {
     uint32_t tmem;
     uint32_t phase;
     int cur_type;
+    float* sP;          // optional: FP32 gathered coefficients [128][ldp] (dot products p_e^T Y_e)
+    double* sDot;       // [npad / 16][128] column-chunk partial dot products
+    int ldp;
 };
 
 // D (128 x npad) = C (tile blocks x K) * K_r^T on the tensor cores for one
@@ -281,8 +293,9 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     }
     tile_setup(a, it, A, base, offs, kTileTC);
     __syncthreads();
+    const bool dots = a.gpart != nullptr && ts.sP != nullptr;
     gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, 0, sh.kpad * sh.esz / 16, ts.sA,
-                         sh.a_plane, tc::sbo_bytes(sh.kpad, sh.esz));
+                         sh.a_plane, tc::sbo_bytes(sh.kpad, sh.esz), dots ? ts.sP : nullptr, ts.ldp);
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();
@@ -322,6 +335,33 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
             dst[1] = make_float4(v[4], v[5], v[6], v[7]);
             dst[2] = make_float4(v[8], v[9], v[10], v[11]);
             dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
+        if (dots && b < it.count) {
+            // this chunk's share of p_e^T Y_e, as a double-FP32 sum in column order
+            DotAcc<float> acc;
+            const float4* pp = reinterpret_cast<const float4*>(ts.sP + b * ts.ldp + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 p4 = pp[q];
+                acc.add(p4.x, v[4 * q]);
+                acc.add(p4.y, v[4 * q + 1]);
+                acc.add(p4.z, v[4 * q + 2]);
+                acc.add(p4.w, v[4 * q + 3]);
+            }
+            ts.sDot[(c0 >> 4) * kTileTC + b] = (double)acc.hi + (double)acc.lo;
+        }
+    }
+    if (dots) {
+        // one partial per 8-block group of the tile: its blocks in order, each
+        // block's column chunks in order (independent of the tile size)
+        __syncthreads();
+        const int ng = (it.count + 7) >> 3, nch = sh.npad >> 4;
+        if (tid < ng) {
+            double sum = 0;
+            const int b1 = min(8 * tid + 8, it.count);
+            for (int bb = 8 * tid; bb < b1; ++bb)
+                for (int c = 0; c < nch; ++c) sum += ts.sDot[c * kTileTC + bb];
+            a.gpart[it.grp + tid] = sum;
         }
     }
     tc::fence_before();

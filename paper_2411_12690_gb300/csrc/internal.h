@@ -88,11 +88,15 @@ struct ArrayDev {            // one array of a (batched) solve
     long long n_dof;         // X*Y*Z*3
     long long block_off;     // first block (site) of this array
     int vwork_off, n_vwork;  // lattice work items of this array
+    int grp_off, n_grp;      // 8-block groups of this array (per-group partial sums of the apply)
     double dT;
 };
 
 struct BlockRef { int array, i, j, type; };            // one site of one array
-struct ApplyWork { int type, array, start, count; };   // blist[start .. start+count)
+// blist[start .. start+count); grp: first 8-block group of the tile (groups are
+// 8 consecutive blist entries of one (array, type) run, numbered over the
+// batch; tiles are multiples of 8 blocks and start on a group)
+struct ApplyWork { int type, array, start, count, grp; };
 struct VecWork { int array, pad; long long start, count; };  // packed lattice DOF range
 
 struct PcgState {            // per-array conjugate-gradient scalars

@@ -737,6 +737,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     s->tc_tile = (int)std::min<int64_t>(kTileTC, std::max<int64_t>(8, round_up((total_blocks + ctx->num_sms - 1) /
                                                                                    ctx->num_sms, 8)));
     int64_t vec_off = 0, block_off = 0;
+    int n_groups = 0;
     for (int a = 0; a < s->n_arrays; ++a) {
         const mstress_layout* L = in[a].L;
         ArrayDev A{};
@@ -772,20 +773,26 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
             }
         // tiles of one type and one array over the same block list: 32 blocks
         // (CUDA-core kernels), tc_tile blocks (tensor-core apply) and 128
-        // blocks (tensor-core recovery)
+        // blocks (tensor-core recovery); every tile size is a multiple of 8,
+        // so a tile starts on an 8-block group of its (array, type) run
+        A.grp_off = n_groups;
         for (int t = 0; t < s->n_types; ++t) {
             auto& v = per_type[t];
             const int start = (int)blist.size();
+            const int grp = n_groups;
             for (int e : v) blist.push_back(e);
             auto tiles = [&](std::vector<ApplyWork>& out, size_t tile) {
                 for (size_t st = 0; st < v.size(); st += tile)
-                    out.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(tile, v.size() - st)});
+                    out.push_back(ApplyWork{t, a, start + (int)st, (int)std::min<size_t>(tile, v.size() - st),
+                                            grp + (int)(st / 8)});
             };
             tiles(awork, kTile64);
             tiles(awork_tc, (size_t)s->tc_tile);
             tiles(awork_rec, kTileTC);
-            if (!v.empty()) s->h_seg.push_back(ApplyWork{t, a, start, (int)v.size()});
+            if (!v.empty()) s->h_seg.push_back(ApplyWork{t, a, start, (int)v.size(), grp});
+            n_groups += (int)((v.size() + 7) / 8);
         }
+        A.n_grp = n_groups - A.grp_off;
         if (any_presc) {
             fixed.resize(vec_off + A.n_dof, 0);
             xbc.resize(vec_off + A.n_dof, 0.0);
@@ -807,6 +814,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     s->n_blocks = block_off;
     MS_REQUIRE(s->n_blocks < (1LL << 31), MSTRESS_EINVAL, "too many blocks");
     s->n_vwork = (int)vwork.size();
+    s->n_grp = n_groups;
     s->n_awork = (int)awork.size();
     s->n_awork_tc = (int)awork_tc.size();
     s->n_awork_rec = (int)awork_rec.size();
@@ -845,6 +853,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     alloc_into(ctx, s->v64.q, nv * sizeof(double), false);
     alloc_into(ctx, s->v64.state, s->n_arrays * sizeof(PcgState));
     alloc_into(ctx, s->part, 3 * (size_t)s->n_vwork * sizeof(double));
+    alloc_into(ctx, s->gpart, (size_t)std::max(1, s->n_grp) * sizeof(double));
     alloc_into(ctx, s->flag, 64);
     alloc_into(ctx, s->tickets, 2 * (size_t)s->n_arrays * sizeof(int));
     alloc_into(ctx, s->timers, 4 * sizeof(unsigned long long));
@@ -884,7 +893,7 @@ void set_tc_tiles(mstress_sol_s* s, int tile) {
     std::vector<ApplyWork> w;
     for (const ApplyWork& g : s->h_seg)
         for (int st = 0; st < g.count; st += tile)
-            w.push_back(ApplyWork{g.type, g.array, g.start + st, std::min(tile, g.count - st)});
+            w.push_back(ApplyWork{g.type, g.array, g.start + st, std::min(tile, g.count - st), g.grp + st / 8});
     if (s->d_awork_tc.bytes < w.size() * sizeof(ApplyWork))
         alloc_into(s->ctx, s->d_awork_tc, w.size() * sizeof(ApplyWork), false);
     MS_CUDA(cudaMemcpyAsync(s->d_awork_tc.ptr, w.data(), w.size() * sizeof(ApplyWork), cudaMemcpyHostToDevice,

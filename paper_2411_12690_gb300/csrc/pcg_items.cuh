@@ -96,44 +96,7 @@ __device__ __forceinline__ void cta_fold8_2(const double* v1, const double* v2, 
     __syncthreads();
 }
 
-// Dot-product accumulators. FP64 vectors: a double. FP32 vectors: a
-// double-FP32 pair (hi + lo) built from error-free transformations on the
-// FP32 pipe (the exact product by fma, the exact sum by TwoSum), about 48
-// significant bits, so the inner PCG's dot products keep FP64-level accuracy
-// without the GPU's narrow FP64 pipe; the pairs are folded in FP64 across
-// warps and work items.
-template <class V>
-struct DotAcc;
-
-template <>
-struct DotAcc<double> {
-    double s = 0;
-    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
-};
-
-template <>
-struct DotAcc<float> {
-    float hi = 0, lo = 0;
-    // (the _rn intrinsics are never contracted into fused operations)
-    __device__ __forceinline__ static void two_sum(float a, float b, float& sum, float& err) {
-        sum = __fadd_rn(a, b);
-        const float bb = __fsub_rn(sum, a);
-        err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
-    }
-    __device__ __forceinline__ void add(float x, float y) {
-        const float p = __fmul_rn(x, y), pe = fmaf(x, y, -p);   // x y = p + pe exactly
-        float sum, err;
-        two_sum(hi, p, sum, err);
-        hi = sum;
-        lo = __fadd_rn(lo, __fadd_rn(err, pe));
-    }
-    __device__ __forceinline__ void merge(float ohi, float olo) {
-        float sum, err;
-        two_sum(hi, ohi, sum, err);
-        hi = sum;
-        lo = __fadd_rn(lo, __fadd_rn(err, olo));
-    }
-};
+using ms::DotAcc;   // dot-product accumulators (solve.h)
 
 // Block sum of double-FP32 accumulators in a fixed order: butterfly of the
 // pairs within each warp, the warp sums (hi + lo in FP64) added in FP64 by
@@ -266,6 +229,73 @@ __device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev
         }
     }
     return acc;
+}
+
+// Interface sum fused with the vector update (the second phase of the
+// two-phase iteration, whose step length alpha = <r,z> / sum_e p_e^T Y_e was
+// folded from the element products): per DOF, p = z + beta p (the same fused
+// multiply-add as the apply's gather), q = sum of the owners' Y_e (masked on
+// constrained rows, never stored), x += alpha p, r -= alpha q, z = D^-1 r; p,
+// x, r, z are stored and this thread's shares of <r,z> and <r,r> returned.
+// Arithmetic in the vector precision V, the same operations as isum_item then
+// vec1_item. U DOFs per thread with all their loads issued first.
+template <int U, class V>
+__device__ __forceinline__ void isum_update_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm,
+                                                 const V* __restrict__ dinv, int ldY, const V* __restrict__ Y,
+                                                 V* __restrict__ p, V* __restrict__ z, V* __restrict__ x,
+                                                 V* __restrict__ r, V beta, V al, DotAcc<V>& srz, DotAcc<V>& srr) {
+    const int n = lm->n, n1 = n - 1;
+    const int16_t* __restrict__ surf = lm->surf_idx;
+    const long long end = it.start + it.count;
+    srz = DotAcc<V>();
+    srr = DotAcc<V>();
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
+        V s[U], dv[U], pv[U], zv[U], xv[U], rv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            s[u] = V(0);
+            dv[u] = V(0);
+            pv[u] = zv[u] = xv[u] = rv[u] = V(0);
+            if (g < end) {
+                dv[u] = dinv[g];
+                pv[u] = p[g];
+                zv[u] = z[g];
+                xv[u] = x[g];
+                rv[u] = r[g];
+                int comp, gx, gy, gz;
+                lattice_coords(A, g, comp, gx, gy, gz);
+                const int ih0 = gx / n1, jh0 = gy / n1;
+                const int ih = min(ih0, A.nx - 1), jh = min(jh0, A.ny - 1);
+                const int il = max((gx % n1 == 0) ? ih0 - 1 : ih0, 0), jl = max((gy % n1 == 0) ? jh0 - 1 : jh0, 0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = (c >> 1) ? jh : jl, i = (c & 1) ? ih : il;
+                    const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
+                    if (use) {
+                        const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
+                        if (sidx >= 0) s[u] += Y[(A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                const V qv = dv[u] != V(0) ? s[u] : V(0);
+                const V pn = p_next(zv[u], pv[u], beta);
+                const V rn = fma(-al, qv, rv[u]);
+                const V zn = dv[u] * rn;
+                p[g] = pn;
+                x[g] = fma(al, pn, xv[u]);
+                r[g] = rn;
+                z[g] = zn;
+                srz.add(rn, zn);
+                srr.add(rn, rn);
+            }
+        }
+    }
 }
 
 // Vector update of one work item: x += alpha p, r -= alpha q, z = D^-1 r in

@@ -1,7 +1,17 @@
 // Persistent cooperative Jacobi-PCG for the global stage (section 4.3, Eq. 20).
 //
 // One cooperative launch runs a whole PCG solve over every array of a batch.
-// Each iteration has three phases separated by a grid barrier:
+// With the resident tensor-core apply (small bases) an iteration has two
+// phases separated by a grid barrier:
+//   A  element products Y_e = A_element p_e (p = z + beta p formed in the
+//      gather) and, in the epilogue, p_e^T Y_e summed per 8-block group;
+//      alpha = <r,z> / sum_e p_e^T Y_e (= <p, A p>) is folded from the group
+//      sums in a fixed order;
+//   B  interface sum and vector update in one pass: p = z + beta p, q = sum_e
+//      G_e^T Y_e (not stored), x += alpha p, r -= alpha q, z = D^-1 r and the
+//      <r,z>, <r,r> partials, folded into beta, the stopping test and the
+//      iteration count.
+// Otherwise an iteration has three phases separated by a grid barrier:
 //   A  element products Y_e = A_element p_e (p = z + beta p formed in the
 //      gather), on FP64 CUDA cores, reduced-precision CUDA cores or tcgen05;
 //   B  interface sum q = sum_e G_e^T Y_e, p stored, <p,q> partials; the CTA that
@@ -40,13 +50,14 @@ struct PcgArgs {
     void *x, *r, *z, *p, *q;
     PcgState* st;
     double *part_pq, *part_rz, *part_rr;
-    int* tickets;              // 2 per array: phase B, phase C
+    int* tickets;              // 2 per array: the alpha fold (phase B, or A when two-phase), the beta fold
     unsigned* bar;             // grid-barrier arrival counter (zero at launch)
     int* n_active;             // arrays still iterating
     int* err;                  // 1: tensor-core wait expired, 2: grid barrier expired
     int* abort;
     int max_loops;
-    unsigned long long* timers;   // optional: ns spent in phases A, B, C and the loop count
+    unsigned long long* timers;   // optional: ns spent in phases A, B, C and the loop count (two-phase
+                                  // iteration: A, B, and C = 0)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     __shared__ double shr[NT / 32], sh8[16];
     __shared__ int s_flag, s_ok, s_active;
     __shared__ unsigned s_kbar;   // grid barriers passed by this CTA
-    __shared__ double s_scalar;
+    __shared__ double s_scalar, s_scalar2;
     __shared__ ArrayDev s_A;
     // one array: every CTA keeps the scalars itself (see below)
     __shared__ double s_rz, s_beta, s_alpha, s_tol2;
@@ -136,11 +147,16 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         tc::fence_after();
         tss.tmem = tmem_base;
     }
+    constexpr bool FUSED = AM == AM_TC;   // two-phase iteration (see the top of this file)
     if constexpr (AM == AM_TC) {
         ts.sB = smem;
         ts.sA = smem + NS * a.sh.b_plane;
+        ts.sP = reinterpret_cast<float*>(ts.sA + NS * a.sh.a_plane);
+        ts.ldp = a.sh.ldp;
+        ts.sDot = reinterpret_cast<double*>(ts.sP + (size_t)kTileTC * a.sh.ldp);
         for (uint32_t i = tid; i < NS * a.sh.a_plane / 16; i += NT)
             reinterpret_cast<uint4*>(ts.sA)[i] = make_uint4(0, 0, 0, 0);
+        for (uint32_t i = tid; i < (uint32_t)kTileTC * a.sh.ldp; i += NT) ts.sP[i] = 0.f;
         if ((tid >> 5) == 0) tc::tmem_alloc_c<128>(&tmem_base);   // npad <= 128 on this path
         if (tid == 0) tc::mbar_init(&mbar, 1);
         tc::fence_before();
@@ -159,20 +175,23 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
 
     // Switch the cursor to array k: report the items finished for the previous
     // array (one atomic; the last reporter folds), then read k's scalars.
-    // phase 1: fold <p,q> into alpha; phase 2: fold <r,z>, <r,r> into beta.
+    // phase 1: fold <p,q> into alpha; phase 2: fold <r,z>, <r,r> into beta;
+    // phase 3 (two-phase iteration, apply): fold the group sums of p_e^T Y_e
+    // into alpha (items counted in 8-block groups).
     auto switch_array = [&](ArrayCursor& cur, int k, int phase) {
         if (cur.k >= 0 && cur.count > 0) {
             const int kk = cur.k;
             if (tid == 0) {
                 __threadfence();
-                const int old = atomicAdd(&a.tickets[2 * kk + phase - 1], cur.count);
-                s_flag = old + cur.count == s_A.n_vwork;
+                const int old = atomicAdd(&a.tickets[2 * kk + (phase == 2 ? 1 : 0)], cur.count);
+                s_flag = old + cur.count == (phase == 3 ? s_A.n_grp : s_A.n_vwork);
             }
             __syncthreads();
             if (s_flag) {
                 __threadfence();
-                if (phase == 1) {
-                    const double pq = pi::cta_fold8(a.part_pq + s_A.vwork_off, s_A.n_vwork, sh8);
+                if (phase != 2) {
+                    const double pq = phase == 3 ? pi::cta_fold8(a.ap.gpart + s_A.grp_off, s_A.n_grp, sh8)
+                                                 : pi::cta_fold8(a.part_pq + s_A.vwork_off, s_A.n_vwork, sh8);
                     if (tid == 0) {
                         a.tickets[2 * kk] = 0;
                         const double al = __ldcg(&a.st[kk].rz) / pq;
@@ -223,7 +242,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             if (tid == 0) {
                 s_A = a.arrays[k];
                 s_active = __ldcg(&a.st[k].active);
-                s_scalar = phase == 1 ? __ldcg(&a.st[k].beta) : __ldcg(&a.st[k].alpha);
+                s_scalar = phase == 2 ? __ldcg(&a.st[k].alpha) : __ldcg(&a.st[k].beta);
+                s_scalar2 = __ldcg(&a.st[k].beta);
             }
             __syncthreads();
         }
@@ -258,14 +278,17 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
         bool failed = false;
+        ArrayCursor curA{solo ? 0 : -1, 0};   // two-phase iteration: groups done per array (alpha fold)
         for (int w = blockIdx.x; w < a.apply_items; w += gridDim.x) {
             if constexpr (AM == AM_TC) {
                 const ApplyWork it = a.ap.work[w];
-                if (!__ldcg(&a.st[it.array].active)) continue;
+                if (!solo && it.array != curA.k) switch_array(curA, it.array, 3);
+                if (!s_active) continue;
                 if (!ai::apply_tc_item<MODE>(a.ap, a.sh, it, ts, base, offs)) {
                     failed = true;
                     break;
                 }
+                curA.count += (it.count + 7) >> 3;
             } else if constexpr (AM == AM_TCS) {
                 break;   // the warp-specialised phase below takes all of the CTA's tiles
             } else {
@@ -283,12 +306,59 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         }
         if constexpr (AM == AM_TCS) failed = !ai::tcs_apply_phase<MODE, false>(a.ap, a.shs, tss, base, offs, blockIdx.x,
                                                                          gridDim.x);
+        if constexpr (FUSED) {
+            if (!solo && !failed) switch_array(curA, -1, 3);
+        }
         if (failed && tid == 0) {
             atomicExch(a.err, 1);
             atomicExch(a.abort, 1);
         }
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 0, t_prev);
+        if constexpr (FUSED) {
+            // ---- alpha from the group sums of p_e^T Y_e (one array: every CTA folds)
+            if (solo && s_active) {
+                const double pq = pi::cta_fold8(a.ap.gpart + s_A.grp_off, s_A.n_grp, sh8);
+                if (tid == 0) {
+                    const double al = s_rz / pq;
+                    if (!(pq > 0) || !isfinite(al)) {
+                        s_alpha = 0.0;
+                        s_active = 0;
+                        if (blockIdx.x == 0) {
+                            a.st[0].alpha = 0.0;
+                            a.st[0].active = 0;
+                            a.st[0].status = MSTRESS_ENUMERIC;
+                            atomicSub(a.n_active, 1);
+                        }
+                    } else {
+                        s_alpha = al;
+                        if (blockIdx.x == 0) a.st[0].alpha = al;
+                    }
+                    s_scalar = s_alpha;
+                    s_scalar2 = s_beta;
+                }
+                __syncthreads();
+            }
+            // ---- phase B: interface sum + vector update, <r,z>, <r,r>
+            ArrayCursor cur{solo ? 0 : -1, 0};
+            for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
+                const VecWork it = a.vwork[w];
+                if (it.array != cur.k) switch_array(cur, it.array, 2);
+                if (!s_active) continue;
+                pi::DotAcc<V> srz, srr;
+                pi::isum_update_item<5, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
+                                           static_cast<const V*>(a.ap.Y), p, z, x, r, (V)s_scalar2, (V)s_scalar, srz,
+                                           srr);
+                const double rz = pi::block_sum(srz, shr);
+                const double rr = pi::block_sum(srr, shr);
+                if (tid == 0) {
+                    a.part_rz[w] = rz;
+                    a.part_rr[w] = rr;
+                }
+                cur.count += 1;
+            }
+            if (!solo) switch_array(cur, -1, 2);
+        } else {
         // ---- phase B: interface sum, <p, q>, alpha
         {
             // one array: the cursor starts on it (s_A, s_active, s_scalar = beta preset)
@@ -351,8 +421,9 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             }
             if (!solo) switch_array(cur, -1, 2);
         }
+        }   // three-phase iteration
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
-        phase_mark(a, 2, t_prev);
+        phase_mark(a, FUSED ? 1 : 2, t_prev);
         if (solo && s_active) {
             double rz, rr;
             pi::cta_fold8_2(a.part_rz + s_A.vwork_off, a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8, rz, rr);
@@ -494,14 +565,16 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
         if (a.sh.tmem_cols > 128) return false;   // the kernel allocates 128 tensor-memory columns
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
+        a.ap.gpart = s->gpart.as<double>();     // two-phase iteration: group sums of p_e^T Y_e
+        const size_t smem = a.sh.smem + a.sh.dot_smem;
         const int need = std::max(a.apply_items, vneed);
         switch (prec) {
             case MSTRESS_TF32:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1>, s, a, a.sh.smem, need, 128);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1>, s, a, smem, need, 128);
             case MSTRESS_BF16:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 1>, s, a, a.sh.smem, need, 128);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 1>, s, a, smem, need, 128);
             default:
-                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 1>, s, a, a.sh.smem, need, 128);
+                return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 1>, s, a, smem, need, 128);
         }
     }
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;

@@ -44,6 +44,7 @@ struct ApplyArgs {
     const void* z;         // optional: gather z + beta x instead of x
     void* Y;               // element products [block][ldY]
     int* err;              // device error word (bounded waits)
+    double* gpart;         // optional: per 8-block group sums of p_e^T Y_e (tensor-core apply)
 };
 
 // The search-direction update p = z + beta p in the vector precision (one
@@ -53,6 +54,45 @@ template <class V>
 __device__ __forceinline__ V p_next(V z, V p, V beta) {
     return fma(beta, p, z);
 }
+
+// Dot-product accumulators. FP64 vectors: a double. FP32 vectors: a
+// double-FP32 pair (hi + lo) built from error-free transformations on the
+// FP32 pipe (the exact product by fma, the exact sum by TwoSum), about 48
+// significant bits, so the inner PCG's dot products keep FP64-level accuracy
+// without the GPU's narrow FP64 pipe; the pairs are folded in FP64 across
+// warps and work items.
+template <class V>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+};
+
+template <>
+struct DotAcc<float> {
+    float hi = 0, lo = 0;
+    // (the _rn intrinsics are never contracted into fused operations)
+    __device__ __forceinline__ static void two_sum(float a, float b, float& sum, float& err) {
+        sum = __fadd_rn(a, b);
+        const float bb = __fsub_rn(sum, a);
+        err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+    }
+    __device__ __forceinline__ void add(float x, float y) {
+        const float p = __fmul_rn(x, y), pe = fmaf(x, y, -p);   // x y = p + pe exactly
+        float sum, err;
+        two_sum(hi, p, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, __fadd_rn(err, pe));
+    }
+    __device__ __forceinline__ void merge(float ohi, float olo) {
+        float sum, err;
+        two_sum(hi, ohi, sum, err);
+        hi = sum;
+        lo = __fadd_rn(lo, __fadd_rn(err, olo));
+    }
+};
 
 // log2 of the smallest power of two >= v (v >= 1): rows spanned by a tile.
 inline int lg_ceil(int v) { return v <= 1 ? 0 : 32 - __builtin_clz((unsigned)(v - 1)); }
@@ -105,6 +145,8 @@ struct mstress_sol_s {
     void* Y64 = nullptr;                  // FP64 element products (Y64own, or Y in FP64 mode)
     ms::DBuf Y;                           // element-by-element products [block][ldY]
     ms::DBuf part;                        // 3 * n_vwork partial sums
+    ms::DBuf gpart;                       // n_grp partial sums of p_e^T Y_e per 8-block group
+    int n_grp = 0;
     ms::DBuf cimg;                        // coefficient images of the tensor-core recovery (reused)
     ms::DBuf flag;                        // device ints: [0] any active, [1] CTA ticket, [2] error,
                                           // [3] loop count, [4] arrays active, [7] abort

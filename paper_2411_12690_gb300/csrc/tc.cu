@@ -35,6 +35,10 @@ ai::TcShape tc_shape(int m, int prec) {
     s.a_plane = (uint32_t)round_up((int64_t)kTileTC * s.kpad * s.esz, 1024);
     s.b_plane = (uint32_t)round_up((int64_t)s.npad * s.kpad * s.esz, 1024);
     s.smem = (size_t)s.ns * (s.a_plane + s.b_plane) + 1024;   // + alignment slack
+    // row stride of the FP32 tile copy: >= both paddings, and 4 more floats
+    // so that eight consecutive rows' 16-byte reads fall in distinct banks
+    s.ldp = (int)round_up(std::max(s.kpad, s.npad), 4) + 4;
+    s.dot_smem = (size_t)kTileTC * s.ldp * sizeof(float) + (size_t)(s.npad / 16) * kTileTC * sizeof(double);
     return s;
 }
 
@@ -111,6 +115,9 @@ __global__ void __launch_bounds__(kTcThreads) k_apply_tc(const __grid_constant__
     ai::TcState ts;
     ts.sB = smem;
     ts.sA = smem + NS * sh.b_plane;
+    ts.sP = nullptr;   // no epilogue dot products in the stand-alone apply
+    ts.sDot = nullptr;
+    ts.ldp = 0;
     for (uint32_t i = tid; i < NS * sh.a_plane / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(ts.sA)[i] = make_uint4(0, 0, 0, 0);
     if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)sh.tmem_cols);
