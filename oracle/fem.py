@@ -335,3 +335,77 @@ def solve_array_fem(block: BoxMesh, site_mat_ids, site_type, dT,
     fixed_dofs = (3 * fixed_nodes[:, None] + np.arange(3)).ravel()
     u = solve_dirichlet(A, dT * b, fixed_dofs, np.zeros(fixed_dofs.size))
     return mesh, u, gauss_stresses(mesh, u, dT, materials)
+
+
+# ------------------------------------- point evaluation (the section 5.1 metric)
+def axis_locate(x: float, length: float, n: int):
+    """Elements of one axis that hold coordinate x of [0, length] cut into n
+    equal elements: [(element, local coordinate in [-1, 1], weight)]. An
+    interior point lies in one element (weight 1); a point on the face shared
+    by two elements takes both, at xi = +1 and -1, weight 1/2 each, so that a
+    field that jumps across the face is read as the mean of its two one-sided
+    limits; the outer faces belong to their one element."""
+    h = length / n
+    t = x / h
+    k = int(round(t))
+    if abs(t - k) <= 1e-9 * max(1.0, abs(t)):
+        sides = [(k - 1, 1.0)] if k - 1 >= 0 else []
+        if k <= n - 1:
+            sides.append((k, -1.0))
+        return [(e, xi, 1.0 / len(sides)) for e, xi in sides]
+    k = min(max(int(np.floor(t)), 0), n - 1)
+    return [(k, 2.0 * (t - k) - 1.0, 1.0)]
+
+
+def point_stresses(mesh: BoxMesh, u: np.ndarray, dT: float, points: np.ndarray,
+                   materials=DEFAULT_MATERIALS) -> np.ndarray:
+    """(n_pts, 6) stress by Eq. 1 at arbitrary points of the mesh, from the
+    nodal displacement u: in the element holding the point, sigma = D B(xi)
+    u_e - alpha (3 lam + 2 mu) dT 1, with B of the trilinear shape functions
+    at the point's local coordinates; on element faces, edges and corners the
+    weighted mean over the elements that meet there (axis_locate per axis)."""
+    en = mesh.element_nodes()
+    h = mesh.h
+    out = np.zeros((points.shape[0], 6))
+    for p, (x, y, z) in enumerate(points):
+        for kx, xi, wx in axis_locate(x, mesh.lx, mesh.ex):
+            for ky, eta, wy in axis_locate(y, mesh.ly, mesh.ey):
+                for kz, zeta, wz in axis_locate(z, mesh.lz, mesh.ez):
+                    e = kx + mesh.ex * (ky + mesh.ey * kz)
+                    B = strain_matrix(shape_gradients(np.array([xi, eta, zeta]), h))
+                    ue = u.reshape(-1, 3)[en[e]].ravel()
+                    mat = materials[int(mesh.mat_id[e])]
+                    sig = elasticity_matrix(mat) @ (B @ ue) - thermal_modulus(mat) * dT * VOIGT_ONE
+                    out[p] += wx * wy * wz * sig
+    return out
+
+
+def midplane_grid(lx: float, ly: float, lz: float, side: int) -> np.ndarray:
+    """(side^2, 3) points of the gridded cut plane of section 5.1 in one unit
+    block: side x side cell-centred points ((i+1/2) lx/side, (j+1/2) ly/side)
+    on the half-height plane z = lz/2, i fastest."""
+    j, i = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
+    return np.stack([(i.ravel() + 0.5) * lx / side, (j.ravel() + 0.5) * ly / side,
+                     np.full(side * side, lz / 2.0)], axis=1)
+
+
+def normalized_mae(vm: np.ndarray, vm_ref: np.ndarray) -> float:
+    """The error measure of section 5.1: mean absolute error of the gridded
+    von Mises stress against the ground truth, divided by the largest ground
+    truth von Mises stress."""
+    vm = np.asarray(vm, dtype=np.float64).ravel()
+    vm_ref = np.asarray(vm_ref, dtype=np.float64).ravel()
+    return float(np.abs(vm - vm_ref).mean() / np.abs(vm_ref).max())
+
+
+def array_grid_vm(amesh: BoxMesh, u: np.ndarray, dT: float, nx: int, ny: int, block_lx: float,
+                  block_ly: float, side: int, materials=DEFAULT_MATERIALS) -> np.ndarray:
+    """(nx*ny, side^2) gridded mid-plane von Mises of a whole-array fine
+    solution (O-FEM), block by block in site order j*nx + i."""
+    g = midplane_grid(block_lx, block_ly, amesh.lz, side)
+    out = []
+    for j in range(ny):
+        for i in range(nx):
+            pts = g + np.array([i * block_lx, j * block_ly, 0.0])
+            out.append(von_mises(point_stresses(amesh, u, dT, pts, materials)))
+    return np.stack(out)

@@ -292,3 +292,21 @@ def recover_vm(blocks: list[ReducedBlock], sol: GlobalSolution, via_modes=True) 
             sig = block_gauss_stress(blk, sol.coeffs[e], sol.dT)
         out.append(fem.element_von_mises(sig))
     return np.stack(out)
+
+
+def recover_vm_grid(blocks: list[ReducedBlock], sol: GlobalSolution, side: int) -> np.ndarray:
+    """(N_blocks, side^2) gridded von Mises on the half-height cut plane of
+    every block (section 5.1): the fine field of Eq. 15, u_e = F [c_e; dT],
+    evaluated point by point with Eq. 1 (fem.point_stresses on the block's
+    own mesh)."""
+    out = []
+    grids = {}
+    for e, t in enumerate(sol.site_type.ravel()):
+        blk = blocks[int(t)]
+        m = blk.mesh
+        key = (m.lx, m.ly, m.lz)
+        if key not in grids:
+            grids[key] = fem.midplane_grid(m.lx, m.ly, m.lz, side)
+        u = block_displacement(blk, sol.coeffs[e], sol.dT)
+        out.append(fem.von_mises(fem.point_stresses(m, u, sol.dT, grids[key])))
+    return np.stack(out)

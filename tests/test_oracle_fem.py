@@ -210,3 +210,69 @@ def test_voxelised_liner_cells_p10():
                 want.add((int(5.5 + sb * b + 0.5), int(5.5 + sa * a + 0.5)))   # (ky, kx)
     got = {(int(ky), int(kx)) for ky, kx in zip(*np.nonzero(lay == 2))}
     assert got == want
+
+
+# ------------------------------------------------ point stresses (section 5.1)
+def _trilinear_field(coords, a):
+    """u = (a0 xyz + a3 x, a1 xyz + a4 y, a2 xyz + a5 z + a6 x): trilinear in
+    x, y, z, so reproduced exactly by Q1 elements on a box mesh."""
+    x, y, z = coords.T
+    return np.stack([a[0] * x * y * z + a[3] * x, a[1] * x * y * z + a[4] * y,
+                     a[2] * x * y * z + a[5] * z + a[6] * x], 1).ravel()
+
+
+def _trilinear_strain(p, a):
+    x, y, z = p
+    return np.array([a[0] * y * z + a[3], a[1] * x * z + a[4], a[2] * x * y + a[5],
+                     a[0] * x * z + a[1] * y * z, a[1] * x * y + a[2] * x * z, a[0] * x * y + a[2] * y * z + a[6]])
+
+
+def test_point_stress_exact_for_trilinear_fields():
+    """Inside each element the stress of a trilinear field is D eps(x) - alpha
+    (3 lam + 2 mu) dT 1 with the exact strain at the point (which varies
+    linearly inside the element), in the element's own material."""
+    rng = np.random.default_rng(3)
+    mesh = fem.BoxMesh(4.0, 3.0, 5.0, 4, 3, 5, rng.integers(0, 3, 60))
+    a = rng.standard_normal(7)
+    u = _trilinear_field(mesh.node_coords(), a)
+    pts = rng.uniform([0, 0, 0], [4.0, 3.0, 5.0], size=(40, 3))
+    sig = fem.point_stresses(mesh, u, -250.0, pts)
+    for p, s in zip(pts, sig):
+        e = int(p[0] // 1.0) + 4 * (int(p[1] // 1.0) + 3 * int(p[2] // 1.0))
+        mat = fem.DEFAULT_MATERIALS[int(mesh.mat_id[e])]
+        ref = fem.elasticity_matrix(mat) @ _trilinear_strain(p, a) + 250.0 * fem.thermal_modulus(mat) * fem.VOIGT_ONE
+        assert np.abs(s - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_point_stress_on_faces_edges_corners_is_the_mean():
+    """On a face between elements of different materials the stress jumps;
+    the point value is the mean over the elements meeting there (2 on a face,
+    4 on an edge, 8 at a corner), each in its own material."""
+    rng = np.random.default_rng(4)
+    mat = rng.integers(0, 3, 8)
+    mesh = fem.BoxMesh(2.0, 2.0, 2.0, 2, 2, 2, mat)
+    a = rng.standard_normal(7)
+    u = _trilinear_field(mesh.node_coords(), a)
+    cases = [((1.0, 0.5, 0.5), [(0, 0, 0), (1, 0, 0)]),
+             ((1.0, 1.0, 0.5), [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0)]),
+             ((1.0, 1.0, 1.0), [(i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]),
+             ((0.0, 0.5, 0.5), [(0, 0, 0)]),                       # outer face: its one element
+             ((2.0, 2.0, 2.0), [(1, 1, 1)])]
+    for p, els in cases:
+        s = fem.point_stresses(mesh, u, 100.0, np.array([p]))[0]
+        eps = _trilinear_strain(np.array(p), a)
+        ref = np.mean([fem.elasticity_matrix(fem.DEFAULT_MATERIALS[int(mat[i + 2 * (j + 2 * k)])]) @ eps
+                       - 100.0 * fem.thermal_modulus(fem.DEFAULT_MATERIALS[int(mat[i + 2 * (j + 2 * k)])])
+                       * fem.VOIGT_ONE for i, j, k in els], axis=0)
+        assert np.abs(s - ref).max() <= 1e-10 * np.abs(ref).max(), p
+
+
+def test_midplane_grid_and_normalized_mae():
+    g = fem.midplane_grid(10.0, 20.0, 50.0, 4)
+    assert g.shape == (16, 3)
+    assert np.allclose(g[:4, 0], [1.25, 3.75, 6.25, 8.75]) and np.allclose(g[::4, 1], [2.5, 7.5, 12.5, 17.5])
+    assert np.all(g[:, 2] == 25.0)
+    ref = np.array([1.0, 4.0, 2.0, 3.0])
+    assert fem.normalized_mae(ref, ref) == 0.0
+    assert fem.normalized_mae(ref + 0.5, ref) == pytest.approx(0.5 / 4.0)
+    assert fem.normalized_mae([0, 4, 2, 3], ref) == pytest.approx(0.25 / 4.0)

@@ -285,3 +285,43 @@ def test_exact_static_condensation_top_clamped():
         ub = mor.block_displacement(blk, sol.coeffs[i], dT).reshape(-1, 3)
         ids = nid[i * ex:(i + 1) * ex + 1, 0:ey + 1, :].transpose(2, 1, 0).ravel()
         assert np.abs(ub - u_fem.reshape(-1, 3)[ids]).max() <= 1e-10 * np.abs(u_fem).max()
+
+
+def test_exact_condensation_gridded_von_mises_equals_fem():
+    """The gridded mid-plane von Mises of section 5.1 (point values of the
+    fine field of Eq. 15) equals O-FEM's at the same points when the reduced
+    basis holds every fine boundary node; the mesh has an even number of
+    layers, so the plane runs along element faces (two-sided means)."""
+    ex, ey, ez = 4, 4, 4
+    tsv = fem.tsv_block_mesh(10.0, 10.0, 20.0, ex, ey, ez, 2.5, 0.5)
+    dum = fem.tsv_block_mesh(10.0, 10.0, 20.0, ex, ey, ez, 0.0, 0.0)
+    nxyz = (ex + 1, ey + 1, ez + 1)
+    blocks = [mor.local_stage(tsv, nxyz), mor.local_stage(dum, nxyz)]
+    st = np.array([[0, 1], [0, 0]])
+    dT = -250.0
+    sol = mor.global_stage(blocks, st, dT)
+    amesh, u_fem, _ = fem.solve_array_fem(tsv, _site_mats(tsv, dum), st, dT)
+    g_mor = mor.recover_vm_grid(blocks, sol, 6)
+    g_fem = fem.array_grid_vm(amesh, u_fem, dT, 2, 2, 10.0, 10.0, 6)
+    assert np.abs(g_mor - g_fem).max() <= 1e-9 * g_fem.max()
+
+
+def test_gridded_error_falls_with_the_basis_order():
+    """The normalised MAE of the gridded von Mises against O-FEM (the error
+    measure of section 5.1 and Table 3) falls as the face order rises."""
+    spec = dict(lx=10.0, ly=10.0, lz=50.0, ex=12, ey=12, ez=10)
+    tsv = fem.tsv_block_mesh(**spec, r_cu=2.5, t_liner=0.5)
+    dum = fem.tsv_block_mesh(**spec, r_cu=0.0, t_liner=0.0)
+    st = np.array([[0, 0], [1, 0]])
+    dT = -250.0
+    amesh, u_fem, _ = fem.solve_array_fem(tsv, _site_mats(tsv, dum), st, dT)
+    ref = fem.array_grid_vm(amesh, u_fem, dT, 2, 2, 10.0, 10.0, 20)
+    errs = []
+    for order in (1, 2, 4):
+        n = order + 1
+        blocks = [mor.local_stage(tsv, (n, n, n)), mor.local_stage(dum, (n, n, n))]
+        sol = mor.global_stage(blocks, st, dT)
+        errs.append(fem.normalized_mae(mor.recover_vm_grid(blocks, sol, 20), ref))
+    print("normalised MAE by order 1, 2, 4:", errs)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.02

@@ -71,3 +71,34 @@ def test_request_stream_is_poisson():
     sides = np.array([r.job.nx for r in reqs])
     assert sides.min() >= 2 and sides.max() <= 128
     assert abs(np.log(sides).mean() - math.log(16.0)) < 0.06  # log-uniform on [2, 128]
+
+
+def test_submodel_recipe():
+    """Scenario 2 (section 5.1): a 15x15 TSV array in two rings of dummy
+    blocks; the synthetic coarse field is prescribed on exactly the lattice
+    points of the six outer faces, is a polynomial of degree <= 2 in the
+    coordinates (so it is smooth across the sub-model) and is seeded."""
+    st = W.submodel_sites(15, 2)
+    assert st.shape == (19, 19) and int((st == 0).sum()) == 225
+    assert np.all(st[:2] == 1) and np.all(st[-2:] == 1) and np.all(st[:, :2] == 1) and np.all(st[:, -2:] == 1)
+    spec = W.BLOCK_SMALL
+    dof, val = W.submodel_boundary(19, 19, spec, seed=5)
+    X = Y = 19 * 2 + 1
+    Z = 3
+    node, comp = dof // 3, dof % 3
+    gx, gy, gz = node % X, (node // X) % Y, node // (X * Y)
+    assert np.all((gx == 0) | (gx == X - 1) | (gy == 0) | (gy == Y - 1) | (gz == 0) | (gz == Z - 1))
+    n_face_points = X * Y * Z - (X - 2) * (Y - 2) * (Z - 2)
+    assert dof.size == 3 * n_face_points and np.unique(dof).size == dof.size
+    # degree <= 2: exact fit by the ten quadratic monomials, per component
+    x, y, z = gx * 5.0, gy * 5.0, gz * 25.0
+    Mq = np.stack([np.ones_like(x), x, y, z, x * x, y * y, z * z, x * y, y * z, z * x], 1).astype(float)
+    for c in range(3):
+        sel = comp == c
+        coef, *_ = np.linalg.lstsq(Mq[sel], val[sel], rcond=None)
+        assert np.abs(Mq[sel] @ coef - val[sel]).max() <= 1e-12 * np.abs(val).max()
+    # magnitude of a thermal mismatch field: alpha_Si |dT| times the half-size
+    assert 1e-3 < np.abs(val).max() < 1.0
+    d2, v2 = W.submodel_boundary(19, 19, spec, seed=5)
+    assert np.array_equal(dof, d2) and np.array_equal(val, v2)
+    assert not np.array_equal(val, W.submodel_boundary(19, 19, spec, seed=6)[1])
