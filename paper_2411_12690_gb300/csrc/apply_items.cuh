@@ -258,6 +258,46 @@ __device__ __forceinline__ void gather_operand(const float* __restrict__ x, cons
     }
 }
 
+// Gather of a tile's coefficients into the K-major no-swizzle operand for
+// its rows [0, count) only: element idx = (kg * count + row) * KE + e takes
+// value e of 16-byte K group kg of block row `row` (consecutive threads fill
+// one row's group, then the next rows, so a warp's stores cover contiguous
+// shared memory). Rows beyond count keep what they held; the MMA rows they
+// produce are never read back. GU values per thread are loaded before any is
+// stored (one round of loads per GU * blockDim.x values). With sP, the FP32
+// values are also kept at sP[row * ldp + k].
+template <int MODE, int GU>
+__device__ __forceinline__ void gather_rows(const float* __restrict__ x, const float* __restrict__ z, float beta,
+                                            int m, int count, const long long* base, const int* offs, int nkg,
+                                            uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo, float* sP, int ldp) {
+    using OM = OperandMap<MODE>;
+    const int total = nkg * count * OM::KE;
+    for (int idx0 = threadIdx.x; idx0 < total; idx0 += (int)blockDim.x * GU) {
+        float v[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = idx0 + u * (int)blockDim.x;
+            v[u] = 0.f;
+            if (idx < total) {
+                const int q = idx >> OM::LGKE, kg = q / count, row = q - kg * count;
+                const int k = (kg << OM::LGKE) + (idx & (OM::KE - 1));
+                if (k < m) v[u] = gather(x, z, base[row] + offs[k], beta);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = idx0 + u * (int)blockDim.x;
+            if (idx < total) {
+                const int e = idx & (OM::KE - 1), q = idx >> OM::LGKE, kg = q / count, row = q - kg * count;
+                const uint32_t off = (uint32_t)(row >> 3) * sbo + (uint32_t)kg * 128u + (uint32_t)(row & 7) * 16u +
+                                     (uint32_t)e * OM::ESZ;
+                put_operand(plane0, plane_bytes, off, v[u], MODE);
+                if (sP) sP[row * ldp + (kg << OM::LGKE) + e] = v[u];
+            }
+        }
+    }
+}
+
 // Per-CTA tensor-core state that persists across work items.
 struct TcState {
     uint8_t* sA;        // gathered coefficients (NS planes)
@@ -269,6 +309,11 @@ struct TcState {
     float* sP;          // optional: FP32 gathered coefficients [128][ldp] (dot products p_e^T Y_e)
     double* sDot;       // [npad / 16][128] column-chunk partial dot products
     int ldp;
+    long long* eidx;    // shared [kTileTC]: block index of each row of the current tile
+    int cached_start;   // tile whose gather set-up (base, offs, eidx) is in shared memory, or -1
+    int cached_array;
+    const ArrayDev* A_pre;   // optional: the array and beta of every tile (one array, kept in
+    const double* beta_pre;  // shared memory by the caller) instead of loading them per tile
 };
 
 // D (128 x npad) = C (tile blocks x K) * K_r^T on the tensor cores for one
@@ -281,21 +326,31 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     const int m = a.m;
-    const ArrayDev A = a.arrays[it.array];
-    const float beta = a.st ? (float)a.st[it.array].beta : 0.f;
     const float* __restrict__ x = static_cast<const float*>(a.x);
     const float* __restrict__ z = static_cast<const float*>(a.z);
     float* __restrict__ Y = static_cast<float*>(a.Y);
+    float beta;
+    if (ts.A_pre) {
+        beta = ts.beta_pre ? (float)*ts.beta_pre : 0.f;
+    } else {
+        beta = a.st ? (float)a.st[it.array].beta : 0.f;
+    }
     if (it.type != ts.cur_type) {
         const uint4* src = static_cast<const uint4*>(a.tt.Klp[it.type]);
         for (uint32_t i = tid; i < NS * sh.b_plane / 16; i += blockDim.x) reinterpret_cast<uint4*>(ts.sB)[i] = src[i];
         ts.cur_type = it.type;
     }
-    tile_setup(a, it, A, base, offs, kTileTC);
+    if (it.start != ts.cached_start || it.array != ts.cached_array) {
+        // the same tile again (a persistent CTA with one tile) keeps its set-up
+        const ArrayDev A = ts.A_pre ? *ts.A_pre : a.arrays[it.array];
+        tile_setup(a, it, A, base, offs, kTileTC, ts.eidx);
+        ts.cached_start = it.start;
+        ts.cached_array = it.array;
+    }
     __syncthreads();
     const bool dots = a.gpart != nullptr && ts.sP != nullptr;
-    gather_operand<MODE>(x, z, beta, m, it.count, base, offs, sh.lg_tile, 0, sh.kpad * sh.esz / 16, ts.sA,
-                         sh.a_plane, tc::sbo_bytes(sh.kpad, sh.esz), dots ? ts.sP : nullptr, ts.ldp);
+    gather_rows<MODE, 12>(x, z, beta, m, it.count, base, offs, sh.kpad * sh.esz / 16, ts.sA, sh.a_plane,
+                          tc::sbo_bytes(sh.kpad, sh.esz), dots ? ts.sP : nullptr, ts.ldp);
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();
@@ -325,7 +380,7 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one block each) and
     // column chunks 16 (w / 4), 16 (w / 4 + nw / 4), ...
     const int b = (warp & 3) * 32 + lane;
-    const long long e = b < it.count ? a.blist[it.start + b] : 0;
+    const long long e = b < it.count ? ts.eidx[b] : 0;
     for (int c0 = 16 * (warp >> 2); c0 < sh.npad; c0 += 16 * (nw >> 2)) {
         float v[16];
         tc::tmem_ld16(ts.tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);

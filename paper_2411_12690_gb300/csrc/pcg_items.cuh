@@ -10,29 +10,31 @@
 namespace ms {
 namespace pi {
 
-// Fixed-order sum of n values by one warp: lane-strided partial sums (four
-// loads in flight, summed in index order), then a butterfly. Loads bypass L1
-// because the values come from other CTAs.
+// Fixed-order sum of n values by one warp: lane-strided partial sums (each
+// lane adds v[lane], v[lane + 32], ... in index order; up to eight loads are
+// issued before they are added), then a butterfly. Loads bypass L1 because
+// the values come from other CTAs.
 __device__ __forceinline__ double warp_fold(const double* v, int n) {
     const int lane = threadIdx.x & 31;
     double s = 0;
-    int i = lane;
-    for (; i + 96 < n; i += 128) {
-        const double a0 = __ldcg(v + i), a1 = __ldcg(v + i + 32), a2 = __ldcg(v + i + 64), a3 = __ldcg(v + i + 96);
-        s += a0;
-        s += a1;
-        s += a2;
-        s += a3;
+    for (int i0 = lane; i0 < n; i0 += 256) {
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = i0 + 32 * u < n ? __ldcg(v + i0 + 32 * u) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + 32 * u < n) s += a[u];
     }
-    for (; i < n; i += 32) s += __ldcg(v + i);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
-// Fixed-order sum of n values by a whole CTA of nw warps: warp w folds the
-// slice [w n / 8, (w+1) n / 8) for w < 8 (warps beyond 8 idle), thread 0 adds
-// the 8 slice sums in order. The order depends only on n, never on which CTA
-// or how many arrays. Result valid in thread 0. Needs all threads.
+// Fixed-order sum of n values by a whole CTA of nw >= 8 warps: warp w folds the
+// slice [w n / 8, (w+1) n / 8) for w < 8 (warps beyond 8 idle), then every
+// thread adds the 8 slice sums in order. The order depends only on n, never
+// on which CTA or how many arrays. Result valid in every thread. Needs all
+// threads; sh8 must not be written again before every thread has returned
+// (the callers pass a barrier first).
 __device__ __forceinline__ double cta_fold8(const double* v, int n, double* sh8) {
     const int w = threadIdx.x >> 5;
     if (w < 8) {
@@ -42,45 +44,21 @@ __device__ __forceinline__ double cta_fold8(const double* v, int n, double* sh8)
     }
     __syncthreads();
     double t = 0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 8; ++k) t += sh8[k];
-    __syncthreads();
+    for (int k = 0; k < 8; ++k) t += sh8[k];
     return t;
 }
 
 // Two fixed-order sums at once (the <r,z> and <r,r> partials of one array):
-// the same slices and order as cta_fold8 for each, with the loads of both in
-// flight together. Results valid in thread 0. Needs all threads.
+// the same slices and order as cta_fold8 for each. Results valid in every
+// thread; sh16 as sh8 above.
 __device__ __forceinline__ void cta_fold8_2(const double* v1, const double* v2, int n, double* sh16, double& t1,
                                             double& t2) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     if (w < 8) {
         const int b = (int)((long long)n * w / 8), e = (int)((long long)n * (w + 1) / 8);
-        double s1 = 0, s2 = 0;
-        int i = b + lane;
-        for (; i + 96 < e; i += 128) {
-            const double a0 = __ldcg(v1 + i), a1 = __ldcg(v1 + i + 32), a2 = __ldcg(v1 + i + 64),
-                         a3 = __ldcg(v1 + i + 96);
-            const double c0 = __ldcg(v2 + i), c1 = __ldcg(v2 + i + 32), c2 = __ldcg(v2 + i + 64),
-                         c3 = __ldcg(v2 + i + 96);
-            s1 += a0;
-            s1 += a1;
-            s1 += a2;
-            s1 += a3;
-            s2 += c0;
-            s2 += c1;
-            s2 += c2;
-            s2 += c3;
-        }
-        for (; i < e; i += 32) {
-            s1 += __ldcg(v1 + i);
-            s2 += __ldcg(v2 + i);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        if (lane == 0) {
+        const double s1 = warp_fold(v1 + b, e - b);
+        const double s2 = warp_fold(v2 + b, e - b);
+        if ((threadIdx.x & 31) == 0) {
             sh16[w] = s1;
             sh16[8 + w] = s2;
         }
@@ -88,12 +66,10 @@ __device__ __forceinline__ void cta_fold8_2(const double* v1, const double* v2, 
     __syncthreads();
     t1 = 0;
     t2 = 0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 8; ++k) {
-            t1 += sh16[k];
-            t2 += sh16[8 + k];
-        }
-    __syncthreads();
+    for (int k = 0; k < 8; ++k) {
+        t1 += sh16[k];
+        t2 += sh16[8 + k];
+    }
 }
 
 using ms::DotAcc;   // dot-product accumulators (solve.h)
@@ -291,6 +267,87 @@ __device__ __forceinline__ void isum_update_item(const VecWork& it, const ArrayD
                 x[g] = fma(al, pn, xv[u]);
                 r[g] = rn;
                 z[g] = zn;
+                srz.add(rn, zn);
+                srr.add(rn, rn);
+            }
+        }
+    }
+}
+
+// Resident vector slice: when a CTA keeps one vector work item for a whole
+// solve, the item's x, r and D^-1 stay in shared memory (only this CTA reads
+// or writes them) and the element-product offsets of each DOF's owners are
+// computed once. resident_setup fills them; resident_update_item is then the
+// same arithmetic as isum_update_item (same owner order, same operations), with
+// only p and z (which the apply of every CTA gathers) in global memory.
+// soff[c * stride + l]: offset into Y of owner c of DOF start + l, or -1.
+template <class V>
+__device__ __forceinline__ void resident_setup(const ArrayDev& A, const LocalMap* lm, int ldY, long long start,
+                                               int count, const V* dinv, const V* x, const V* r, V* sd, V* sx,
+                                               V* sr, int* soff, int stride) {
+    const int n = lm->n, n1 = n - 1;
+    const int16_t* __restrict__ surf = lm->surf_idx;
+    for (int l = threadIdx.x; l < count; l += blockDim.x) {
+        const long long g = start + l;
+        sd[l] = dinv[g];
+        sx[l] = x[g];
+        sr[l] = r[g];
+        int comp, gx, gy, gz;
+        lattice_coords(A, g, comp, gx, gy, gz);
+        const int ih0 = gx / n1, jh0 = gy / n1;
+        const int ih = min(ih0, A.nx - 1), jh = min(jh0, A.ny - 1);
+        const int il = max((gx % n1 == 0) ? ih0 - 1 : ih0, 0), jl = max((gy % n1 == 0) ? jh0 - 1 : jh0, 0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = (c >> 1) ? jh : jl, i = (c & 1) ? ih : il;
+            const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
+            int off = -1;
+            if (use) {
+                const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
+                if (sidx >= 0) off = (int)((A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp);
+            }
+            soff[c * stride + l] = off;
+        }
+    }
+}
+
+template <int U, class V>
+__device__ __forceinline__ void resident_update_item(long long start, int count, const int* __restrict__ soff,
+                                                     int stride, const V* sd, V* sx, V* sr, const V* __restrict__ Y,
+                                                     V* __restrict__ p, V* __restrict__ z, V beta, V al,
+                                                     DotAcc<V>& srz, DotAcc<V>& srr) {
+    srz = DotAcc<V>();
+    srr = DotAcc<V>();
+    for (int l0 = threadIdx.x; l0 < count; l0 += (int)blockDim.x * U) {
+        V s[U], pv[U], zv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int l = l0 + u * (int)blockDim.x;
+            s[u] = V(0);
+            pv[u] = zv[u] = V(0);
+            if (l < count) {
+                pv[u] = p[start + l];
+                zv[u] = z[start + l];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int off = soff[c * stride + l];
+                    if (off >= 0) s[u] += Y[off];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int l = l0 + u * (int)blockDim.x;
+            if (l < count) {
+                const V dv = sd[l];
+                const V qv = dv != V(0) ? s[u] : V(0);
+                const V pn = p_next(zv[u], pv[u], beta);
+                const V rn = fma(-al, qv, sr[l]);
+                const V zn = dv * rn;
+                p[start + l] = pn;
+                z[start + l] = zn;
+                sx[l] = fma(al, pn, sx[l]);
+                sr[l] = rn;
                 srz.add(rn, zn);
                 srr.add(rn, rn);
             }

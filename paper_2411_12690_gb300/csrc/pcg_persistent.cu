@@ -56,6 +56,7 @@ struct PcgArgs {
     int* err;                  // 1: tensor-core wait expired, 2: grid barrier expired
     int* abort;
     int max_loops;
+    int resident;              // two-phase iteration, one array: vector slices may stay in shared memory
     unsigned long long* timers;   // optional: ns spent in phases A, B, C and the loop count (two-phase
                                   // iteration: A, B, and C = 0)
 };
@@ -121,7 +122,7 @@ template <class V, int AM, int MODE, int RPT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArgs a) {
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    __shared__ long long base[kTileTC];
+    __shared__ long long base[kTileTC], s_eidx[kTileTC];
     __shared__ __align__(16) int offs[3 * kMaxSurf];
     __shared__ double shr[NT / 32], sh8[16];
     __shared__ int s_flag, s_ok, s_active;
@@ -166,6 +167,11 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         ts.mbar = &mbar;
         ts.phase = 0;
         ts.cur_type = -1;
+        ts.eidx = s_eidx;
+        ts.cached_start = -1;
+        ts.cached_array = -1;
+        ts.A_pre = nullptr;
+        ts.beta_pre = nullptr;
     }
     V* x = static_cast<V*>(a.x);
     V* r = static_cast<V*>(a.r);
@@ -260,6 +266,40 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     // streamed tensor-core apply, whose registers are fully used and whose
     // workloads are batches.)
     const bool solo = AM != AM_TCS && a.n_arrays == 1;
+    if constexpr (AM == AM_TC) {
+        if (solo) {   // one array: its descriptor and beta come from this CTA's shared copies
+            ts.A_pre = &s_A;
+            ts.beta_pre = &s_beta;
+        }
+    }
+    // Resident vector slice (two-phase iteration, one array, at most one vector
+    // work item per CTA): the CTA's item never changes during the solve, so its
+    // x, r, D^-1 and owner offsets live in shared memory (after the tensor-core
+    // buffers) and only p and z go through global memory.
+    const bool resident = FUSED && solo && a.resident && a.n_vwork <= (int)gridDim.x;
+    V *sVd = nullptr, *sVx = nullptr, *sVr = nullptr;
+    int* sOff = nullptr;
+    long long v_start = 0;
+    int v_count = 0;
+    if constexpr (FUSED) {
+        if (resident) {
+            uint8_t* q0 = reinterpret_cast<uint8_t*>(ts.sDot + (size_t)(a.sh.npad / 16) * kTileTC);
+            sVd = reinterpret_cast<V*>(q0);
+            sVx = sVd + kVecChunkTC;
+            sVr = sVx + kVecChunkTC;
+            sOff = reinterpret_cast<int*>(sVr + kVecChunkTC);
+            if ((int)blockIdx.x < a.n_vwork) {
+                const VecWork it = a.vwork[blockIdx.x];
+                v_start = it.start;
+                v_count = (int)it.count;
+                if (tid == 0) s_A = a.arrays[0];
+                __syncthreads();
+                pi::resident_setup<V>(s_A, a.lm, a.ap.ldY, v_start, v_count, static_cast<const V*>(a.dinv), x, r,
+                                      sVd, sVx, sVr, sOff, kVecChunkTC);
+            }
+            __syncthreads();
+        }
+    }
     if (tid == 0) {
         s_kbar = 0;   // read first by thread 0 itself in the first barrier
         if (solo) {
@@ -341,6 +381,20 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             }
             // ---- phase B: interface sum + vector update, <r,z>, <r,r>
             ArrayCursor cur{solo ? 0 : -1, 0};
+            if (resident) {
+                if ((int)blockIdx.x < a.n_vwork && s_active) {
+                    pi::DotAcc<V> srz, srr;
+                    pi::resident_update_item<5, V>(v_start, v_count, sOff, kVecChunkTC, sVd, sVx, sVr,
+                                                   static_cast<const V*>(a.ap.Y), p, z, (V)s_scalar2, (V)s_scalar,
+                                                   srz, srr);
+                    const double rz = pi::block_sum(srz, shr);
+                    const double rr = pi::block_sum(srr, shr);
+                    if (tid == 0) {
+                        a.part_rz[blockIdx.x] = rz;
+                        a.part_rr[blockIdx.x] = rr;
+                    }
+                }
+            } else
             for (int w = blockIdx.x; w < a.n_vwork; w += gridDim.x) {
                 const VecWork it = a.vwork[w];
                 if (it.array != cur.k) switch_array(cur, it.array, 2);
@@ -459,6 +513,15 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         if (a.timers && blockIdx.x == 0 && tid == 0) a.timers[3] += 1;
         if (solo ? !s_active : *(volatile int*)a.n_active <= 0) break;
     }
+    if constexpr (FUSED) {
+        if (resident && (int)blockIdx.x < a.n_vwork) {   // the slice's x and r back to global memory
+            __syncthreads();
+            for (int l = tid; l < v_count; l += NT) {
+                x[v_start + l] = sVx[l];
+                r[v_start + l] = sVr[l];
+            }
+        }
+    }
     if constexpr (AM == AM_TC) {
         if (*(volatile int*)a.abort) tc::mbar_wait(&mbar, ts.phase ^ 1u, 1 << 20);   // bounded drain
         tc::fence_before();
@@ -566,7 +629,13 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
         a.ap.gpart = s->gpart.as<double>();     // two-phase iteration: group sums of p_e^T Y_e
-        const size_t smem = a.sh.smem + a.sh.dot_smem;
+        size_t smem = a.sh.smem + a.sh.dot_smem;
+        // resident vector slices: one array whose element-product offsets fit in 32 bits
+        const size_t vec_smem = (size_t)kVecChunkTC * (3 * sizeof(float) + 4 * sizeof(int));
+        if (s->n_arrays == 1 && (int64_t)s->n_blocks * s->ldY < (1LL << 31) && smem + vec_smem <= 200 * 1024) {
+            a.resident = 1;
+            smem += vec_smem;
+        }
         const int need = std::max(a.apply_items, vneed);
         switch (prec) {
             case MSTRESS_TF32:

@@ -100,8 +100,9 @@ inline int lg_ceil(int v) { return v <= 1 ? 0 : 32 - __builtin_clz((unsigned)(v 
 // Per-tile gather set-up: lattice base index of each block of the tile and
 // the per-array offset of each element DOF (Lagrange node (a, b, c) of the
 // block sits on lattice point (i(n-1)+a, j(n-1)+b, c)).
+// With eidx, the block index of each tile row is kept as well.
 __device__ __forceinline__ void tile_setup(const ApplyArgs& a, const ApplyWork& it, const ArrayDev& A,
-                                           long long* base, int* offs, int tile) {
+                                           long long* base, int* offs, int tile, long long* eidx = nullptr) {
     const int n1 = a.lm->n - 1;
     for (int k = threadIdx.x; k < a.m; k += blockDim.x) {
         int q = k / 3, c = k - 3 * q;
@@ -109,8 +110,10 @@ __device__ __forceinline__ void tile_setup(const ApplyArgs& a, const ApplyWork& 
     }
     for (int t = threadIdx.x; t < tile; t += blockDim.x)
         if (t < it.count) {
-            BlockRef br = a.bref[a.blist[it.start + t]];
+            const int e = a.blist[it.start + t];
+            BlockRef br = a.bref[e];
             base[t] = A.vec_off + 3LL * ((long long)br.j * n1 * A.X + (long long)br.i * n1);
+            if (eidx) eidx[t] = e;
         }
 }
 

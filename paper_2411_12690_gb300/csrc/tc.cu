@@ -118,6 +118,12 @@ __global__ void __launch_bounds__(kTcThreads) k_apply_tc(const __grid_constant__
     ts.sP = nullptr;   // no epilogue dot products in the stand-alone apply
     ts.sDot = nullptr;
     ts.ldp = 0;
+    __shared__ long long eidx[kTileTC];
+    ts.eidx = eidx;
+    ts.cached_start = -1;
+    ts.cached_array = -1;
+    ts.A_pre = nullptr;
+    ts.beta_pre = nullptr;
     for (uint32_t i = tid; i < NS * sh.a_plane / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(ts.sA)[i] = make_uint4(0, 0, 0, 0);
     if ((tid >> 5) == 0) tc::tmem_alloc(&tmem_base, (uint32_t)sh.tmem_cols);
