@@ -177,8 +177,22 @@ int mstress_block_import(mstress_ctx ctx, const mstress_block_mesh* mesh, int or
 #define MSTRESS_BLOCK_S      2   /* 48*n_el*(m+1) */
 #define MSTRESS_BLOCK_F      3   /* n_dof*(m+1)  */
 #define MSTRESS_BLOCK_SMEAN  4   /* 6*n_el*(m+1): Gauss mean of S, row e*6+comp */
+#define MSTRESS_BLOCK_SGRID  5   /* 6*side^2*(m+1): grid modes (mstress_block_grid), row p*6+comp */
 /* Copy one block array to host memory (count = number of doubles in dst). */
 int mstress_block_export(mstress_block blk, int what, double* dst, size_t count);
+/* Gridded cut-plane output (the error measure of section 5.1 samples the von
+   Mises stress on the plane through the half height of the blocks, on a
+   100 x 100 grid per block). Builds the block's grid modes for side x side
+   cell-centred points ((i + 1/2) lx/side, (j + 1/2) ly/side, lz/2), point
+   p = i + side*j: the stress of Eq. 1 of every basis column of Eq. 15 at the
+   point, evaluated in the fine element that holds it (trilinear shape
+   functions at the point's local coordinates); a point on faces shared by
+   elements takes the mean over those elements (the mean of the one-sided
+   values of a stress that jumps there). Needs a block from
+   mstress_build_block (materials and basis kept on the device); 1 <= side <=
+   400; a later call with another side replaces the grid. Enables recovery
+   output MSTRESS_VM_GRID for solutions whose blocks all have the same grid. */
+int mstress_block_grid(mstress_block blk, int side);
 /* m (element DOFs), n_el (fine elements), n_dof (fine DOFs), cg_iters (local stage). */
 int mstress_block_info(mstress_block blk, int* m, int* n_el, int* n_dof, int* cg_iters);
 /* Free a block model. Work the library issued on the context's stream is
@@ -211,12 +225,15 @@ int mstress_solve_batch(mstress_ctx ctx, const mstress_layout* layouts, const do
      SIGMA_GP  [block][n_el*48]        Gauss-point stress S [c_e; dT] (Eq. 15 + Eq. 1);
                FP64 / FP32 as VM_ELEM
      U_NODE    FP64  [block][n_dof]    fine displacement F [c_e; dT] (Eq. 15)
-     LATTICE   FP64  [X*Y*Z*3]         the global DOF vector u of Eq. 20 per array */
+     LATTICE   FP64  [X*Y*Z*3]         the global DOF vector u of Eq. 20 per array
+     VM_GRID   [block][side^2]         von Mises on the half-height cut plane at the
+               points of mstress_block_grid (section 5.1); FP64 / FP32 as VM_ELEM */
 #define MSTRESS_COEFF    0
 #define MSTRESS_VM_ELEM  1
 #define MSTRESS_SIGMA_GP 2
 #define MSTRESS_U_NODE   3
 #define MSTRESS_LATTICE  4
+#define MSTRESS_VM_GRID  5
 /* Size in bytes that mstress_recover(what) writes for this solution. */
 int mstress_recover_size(mstress_sol sol, int what, size_t* bytes);
 /* Compute and write one recovery output into dst (device memory if

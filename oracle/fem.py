@@ -357,27 +357,32 @@ def axis_locate(x: float, length: float, n: int):
     return [(k, 2.0 * (t - k) - 1.0, 1.0)]
 
 
-def point_stresses(mesh: BoxMesh, u: np.ndarray, dT: float, points: np.ndarray,
+def point_stresses(mesh: BoxMesh, u: np.ndarray, dT, points: np.ndarray,
                    materials=DEFAULT_MATERIALS) -> np.ndarray:
-    """(n_pts, 6) stress by Eq. 1 at arbitrary points of the mesh, from the
-    nodal displacement u: in the element holding the point, sigma = D B(xi)
-    u_e - alpha (3 lam + 2 mu) dT 1, with B of the trilinear shape functions
-    at the point's local coordinates; on element faces, edges and corners the
-    weighted mean over the elements that meet there (axis_locate per axis)."""
+    """Stress by Eq. 1 at arbitrary points of the mesh, from the nodal
+    displacement u: in the element holding the point, sigma = D B(xi) u_e -
+    alpha (3 lam + 2 mu) dT 1, with B of the trilinear shape functions at the
+    point's local coordinates; on element faces, edges and corners the
+    weighted mean over the elements that meet there (axis_locate per axis).
+    u (n_dof,) with a scalar dT gives (n_pts, 6); u (n_dof, k) with dT of
+    length k (one load per column) gives (n_pts, 6, k)."""
     en = mesh.element_nodes()
     h = mesh.h
-    out = np.zeros((points.shape[0], 6))
+    single = u.ndim == 1
+    U = u.reshape(-1, 3, 1) if single else u.reshape(-1, 3, u.shape[1])
+    dTs = np.atleast_1d(np.asarray(dT, dtype=np.float64))
+    out = np.zeros((points.shape[0], 6, U.shape[2]))
     for p, (x, y, z) in enumerate(points):
         for kx, xi, wx in axis_locate(x, mesh.lx, mesh.ex):
             for ky, eta, wy in axis_locate(y, mesh.ly, mesh.ey):
                 for kz, zeta, wz in axis_locate(z, mesh.lz, mesh.ez):
                     e = kx + mesh.ex * (ky + mesh.ey * kz)
                     B = strain_matrix(shape_gradients(np.array([xi, eta, zeta]), h))
-                    ue = u.reshape(-1, 3)[en[e]].ravel()
+                    ue = U[en[e]].reshape(24, -1)
                     mat = materials[int(mesh.mat_id[e])]
-                    sig = elasticity_matrix(mat) @ (B @ ue) - thermal_modulus(mat) * dT * VOIGT_ONE
+                    sig = elasticity_matrix(mat) @ (B @ ue) - thermal_modulus(mat) * np.outer(VOIGT_ONE, dTs)
                     out[p] += wx * wy * wz * sig
-    return out
+    return out[:, :, 0] if single else out
 
 
 def midplane_grid(lx: float, ly: float, lz: float, side: int) -> np.ndarray:

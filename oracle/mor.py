@@ -310,3 +310,13 @@ def recover_vm_grid(blocks: list[ReducedBlock], sol: GlobalSolution, side: int) 
         u = block_displacement(blk, sol.coeffs[e], sol.dT)
         out.append(fem.von_mises(fem.point_stresses(m, u, sol.dT, grids[key])))
     return np.stack(out)
+
+
+def grid_stress_modes(block: ReducedBlock, side: int) -> np.ndarray:
+    """(side^2, 6, m+1) stress of every basis column of Eq. 15 at the
+    half-height grid points (Eq. 1; column m is f_T with dT = 1, so it holds
+    the thermal term): sigma at point p = modes[p] @ [c; dT]."""
+    m = block.mesh
+    loads = np.zeros(block.m + 1)
+    loads[-1] = 1.0
+    return fem.point_stresses(m, block.F, loads, fem.midplane_grid(m.lx, m.ly, m.lz, side))

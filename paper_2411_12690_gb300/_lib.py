@@ -29,12 +29,14 @@ MSTRESS_BLOCK_BR = 1
 MSTRESS_BLOCK_S = 2
 MSTRESS_BLOCK_F = 3
 MSTRESS_BLOCK_SMEAN = 4
+MSTRESS_BLOCK_SGRID = 5
 
 MSTRESS_COEFF = 0
 MSTRESS_VM_ELEM = 1
 MSTRESS_SIGMA_GP = 2
 MSTRESS_U_NODE = 3
 MSTRESS_LATTICE = 4
+MSTRESS_VM_GRID = 5
 
 MSTRESS_RQ_QUEUED = 0
 MSTRESS_RQ_RUNNING = 1
@@ -97,6 +99,7 @@ SIGNATURES = {
     "mstress_block_import": (I, [P, C.POINTER(mstress_block_mesh), I, PD, PD, PD, PD, C.POINTER(P)]),
     "mstress_block_export": (I, [P, I, PD, C.c_size_t]),
     "mstress_block_info": (I, [P, PI, PI, PI, PI]),
+    "mstress_block_grid": (I, [P, I]),
     "mstress_free_block": (None, [P]),
     "mstress_solve": (I, [P, C.POINTER(mstress_layout), C.c_double, C.POINTER(mstress_bc), C.POINTER(P)]),
     "mstress_solve_batch": (I, [P, C.POINTER(mstress_layout), PD, C.POINTER(mstress_bc), I, C.POINTER(P)]),

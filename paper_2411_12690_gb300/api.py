@@ -201,11 +201,19 @@ class Block:
         self.ctx._check(self.ctx.lib.mstress_block_info(self.h, *[C.byref(v) for v in vals]))
         return dict(zip(("m", "n_el", "n_dof", "cg_iters"), [v.value for v in vals]))
 
+    def grid(self, side: int = 100) -> "Block":
+        """Build the grid modes of the half-height cut plane (side x side points)."""
+        self.ctx._check(self.ctx.lib.mstress_block_grid(self.h, side))
+        self.grid_side = side
+        return self
+
     def export(self, what: int) -> np.ndarray:
         inf = self.info()
         m, n_el, n_dof = inf["m"], inf["n_el"], inf["n_dof"]
+        ng = getattr(self, "grid_side", 0) ** 2
         shape = {L.MSTRESS_BLOCK_KR: (m, m), L.MSTRESS_BLOCK_BR: (m,), L.MSTRESS_BLOCK_S: (48 * n_el, m + 1),
-                 L.MSTRESS_BLOCK_F: (n_dof, m + 1), L.MSTRESS_BLOCK_SMEAN: (6 * n_el, m + 1)}[what]
+                 L.MSTRESS_BLOCK_F: (n_dof, m + 1), L.MSTRESS_BLOCK_SMEAN: (6 * n_el, m + 1),
+                 L.MSTRESS_BLOCK_SGRID: (6 * ng, m + 1)}[what]
         out = np.empty(shape, dtype=np.float64)
         self.ctx._check(self.ctx.lib.mstress_block_export(self.h, what, _f64(out), out.size))
         return out
@@ -258,7 +266,7 @@ class Solution:
         reduced-precision VM_ELEM / SIGMA_GP)."""
         nbytes = self.recover_size(what)
         if out is None:
-            fp32 = (what in (L.MSTRESS_VM_ELEM, L.MSTRESS_SIGMA_GP)
+            fp32 = (what in (L.MSTRESS_VM_ELEM, L.MSTRESS_SIGMA_GP, L.MSTRESS_VM_GRID)
                     and self.ctx.opts.precision != L.MSTRESS_FP64)
             out = np.empty(nbytes // (4 if fp32 else 8), dtype=np.float32 if fp32 else np.float64)
         if isinstance(out, np.ndarray):

@@ -328,6 +328,9 @@ int mstress_block_export(mstress_block blk, int what, double* dst, size_t count)
         case MSTRESS_BLOCK_BR: src = blk->br.ptr; rows = 1; cols = m; spitch = m; break;
         case MSTRESS_BLOCK_S: src = blk->S.ptr; rows = (size_t)48 * blk->n_el; cols = m1; spitch = ld; break;
         case MSTRESS_BLOCK_SMEAN: src = blk->Smean.ptr; rows = (size_t)6 * blk->n_el; cols = m1; spitch = ld; break;
+        case MSTRESS_BLOCK_SGRID:
+            MS_REQUIRE(blk->n_grid > 0, MSTRESS_EINVAL, "no grid modes: call mstress_block_grid first");
+            src = blk->Sgrid.ptr; rows = (size_t)6 * blk->n_grid; cols = m1; spitch = ld; break;
         case MSTRESS_BLOCK_F:
             MS_REQUIRE(blk->has_F, MSTRESS_EINVAL, "block holds no basis F");
             src = blk->F.ptr; rows = blk->n_dof; cols = m1; spitch = ld; break;
@@ -336,6 +339,15 @@ int mstress_block_export(mstress_block blk, int what, double* dst, size_t count)
     MS_REQUIRE(count >= rows * cols, MSTRESS_EINVAL, "dst too small");
     MS_CUDA(cudaMemcpy2DAsync(dst, cols * sizeof(double), src, spitch * sizeof(double), cols * sizeof(double),
                               rows, cudaMemcpyDeviceToHost, ctx->stream));
+    MS_CUDA(cudaStreamSynchronize(ctx->stream));
+    MS_API_END(ctx)
+}
+
+int mstress_block_grid(mstress_block blk, int side) {
+    if (!blk) return MSTRESS_EINVAL;
+    mstress_ctx ctx = blk->ctx;
+    MS_API_BEGIN
+    build_grid_modes(blk, side);
     MS_CUDA(cudaStreamSynchronize(ctx->stream));
     MS_API_END(ctx)
 }

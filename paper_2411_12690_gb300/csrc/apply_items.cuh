@@ -23,9 +23,11 @@ namespace ai {
 __device__ __forceinline__ float round_tf32(float v) { return tc::to_tf32(v); }
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
+// Loads go through L2 (ld.global.cg): other CTAs of a persistent solve write
+// these vectors between grid barriers.
 template <class V>
 __device__ __forceinline__ V gather(const V* x, const V* z, long long g, V beta) {
-    return z ? p_next(z[g], x[g], beta) : x[g];
+    return z ? p_next(__ldcg(z + g), __ldcg(x + g), beta) : __ldcg(x + g);
 }
 
 // Gather the element DOFs of a tile of (1 << tile_shift) blocks, index
@@ -407,15 +409,22 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
         }
     }
     if (dots) {
-        // one partial per 8-block group of the tile: its blocks in order, each
-        // block's column chunks in order (independent of the tile size)
+        // one partial per 8-block group of the tile: each block's column
+        // chunks summed in order, then the group's blocks in order
+        // (independent of the tile size)
         __syncthreads();
-        const int ng = (it.count + 7) >> 3, nch = sh.npad >> 4;
+        const int nch = sh.npad >> 4;
+        if (tid < it.count) {
+            double sb = 0;
+            for (int c = 0; c < nch; ++c) sb += ts.sDot[c * kTileTC + tid];
+            ts.sDot[tid] = sb;   // chunk 0's slot of this block, read only by this thread above
+        }
+        __syncthreads();
+        const int ng = (it.count + 7) >> 3;
         if (tid < ng) {
             double sum = 0;
             const int b1 = min(8 * tid + 8, it.count);
-            for (int bb = 8 * tid; bb < b1; ++bb)
-                for (int c = 0; c < nch; ++c) sum += ts.sDot[c * kTileTC + bb];
+            for (int bb = 8 * tid; bb < b1; ++bb) sum += ts.sDot[bb];
             a.gpart[it.grp + tid] = sum;
         }
     }

@@ -159,6 +159,14 @@ struct mstress_block_s {
     ms::DBuf Kr_lp[4], Smean_lp[4], S_lp[4];
     // tensor-core operand images (K-major, no-swizzle core-matrix layout), by precision mode
     ms::DBuf Kr_tc[4], Smean_tc[4];
+    // fine-mesh materials (kept from the local stage; absent for imported blocks)
+    bool has_mat = false;
+    ms::DBuf mat_id;                       // n_el material indices
+    double mat_lam[ms::kMaxMat] = {}, mat_mu[ms::kMaxMat] = {}, mat_tm[ms::kMaxMat] = {};
+    // stress modes at the points of the half-height cut plane (gridded output)
+    int grid_side = 0, n_grid = 0;         // side x side points, or none
+    ms::DBuf Sgrid;                        // (6 n_grid) x ld FP64, row p*6+comp
+    ms::DBuf Sgrid_lp[4], Sgrid_tc[4];     // low-precision copies / tensor-core images
 };
 
 namespace ms {
@@ -169,6 +177,7 @@ void alloc_into(mstress_ctx ctx, DBuf& b, size_t bytes, bool zero = true);
 int build_block(mstress_ctx ctx, const mstress_block_mesh* mesh, const mstress_tsv_geom* tsv,
                 const mstress_material* mats, int n_mat, int order, mstress_block* out);
 void block_compute_smean(mstress_block blk);
+void build_grid_modes(mstress_block blk, int side);   // Sgrid of the half-height plane
 
 // low-precision operand preparation (tensor-core paths) --------------------
 void ensure_lowp(mstress_block blk, int precision);

@@ -493,6 +493,100 @@ __global__ void k_stress_modes(Mesh M, const uint8_t* mat, const double* Bg_g, M
     for (int r = 0; r < 6; ++r) Smean[((size_t)e * 6 + r) * ld + col] = mean[r] * 0.125;
 }
 
+// Elements of one axis holding coordinate x of [0, len] cut into ne equal
+// elements: one element and its local coordinate in [-1, 1], or, on a face
+// shared by two elements, both (at +1 and -1, weight 1/2 each), so that a
+// stress that jumps across the face is read as the mean of its two one-sided
+// values (the outer faces belong to their one element).
+struct AxisPick {
+    int n;
+    int e[2];
+    double xi[2];
+    double w;
+};
+
+__device__ AxisPick axis_pick(double x, double len, int ne) {
+    const double t = x / (len / ne);
+    const double k = rint(t);
+    AxisPick a;
+    a.n = 0;
+    if (fabs(t - k) <= 1e-9 * fmax(1.0, fabs(t))) {
+        const int kk = (int)k;
+        if (kk - 1 >= 0) { a.e[a.n] = kk - 1; a.xi[a.n] = 1.0; ++a.n; }
+        if (kk <= ne - 1) { a.e[a.n] = kk; a.xi[a.n] = -1.0; ++a.n; }
+        a.w = 1.0 / a.n;
+    } else {
+        int kk = (int)floor(t);
+        kk = min(max(kk, 0), ne - 1);
+        a.n = 1;
+        a.e[0] = kk;
+        a.xi[0] = 2.0 * (t - kk) - 1.0;
+        a.w = 1.0;
+    }
+    return a;
+}
+
+// Stress modes at the points of the half-height cut plane (the gridded output
+// of section 5.1): point p = i + side j at ((i + 1/2) lx / side, (j + 1/2) ly /
+// side, lz / 2), basis column col: Sg[(p*6 + r)*ld + col] = (D B(xi) F_e)[r]
+// of Eq. 1 in the element holding the point (minus alpha (3 lam + 2 mu) for
+// the f_T column, which carries dT = 1), with B the strain of the trilinear
+// shape functions at the point's local coordinates; on element faces the
+// weighted mean over the elements meeting there (axis_pick per axis).
+__global__ void k_grid_modes(Mesh M, const uint8_t* mat, MatTab mt, int m, int ld, const double* F, int side,
+                             double lx, double ly, double lz, double* Sg) {
+    const int p = blockIdx.x;
+    const int col = blockIdx.y * blockDim.x + threadIdx.x;
+    if (col > m) return;
+    const int i = p % side, j = p / side;
+    const AxisPick ax = axis_pick((i + 0.5) * lx / side, lx, M.ex);
+    const AxisPick ay = axis_pick((j + 0.5) * ly / side, ly, M.ey);
+    const AxisPick az = axis_pick(0.5 * lz, lz, M.ez);
+    const double h[3] = {lx / M.ex, ly / M.ey, lz / M.ez};
+    double sig[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < ax.n; ++a)
+        for (int b = 0; b < ay.n; ++b)
+            for (int c = 0; c < az.n; ++c) {
+                const int kx = ax.e[a], ky = ay.e[b], kz = az.e[c];
+                const double xi[3] = {ax.xi[a], ay.xi[b], az.xi[c]};
+                const double w = ax.w * ay.w * az.w;
+                double eps[6] = {0, 0, 0, 0, 0, 0};
+                for (int l = 0; l < 8; ++l) {
+                    const double sgn[3] = {double(2 * (l & 1) - 1), double(2 * ((l >> 1) & 1) - 1),
+                                           double(2 * ((l >> 2) & 1) - 1)};
+                    double f[3], g[3];
+                    for (int d = 0; d < 3; ++d) f[d] = 0.5 * (1.0 + sgn[d] * xi[d]);
+                    for (int d = 0; d < 3; ++d) {
+                        double q = 0.5 * sgn[d] * (2.0 / h[d]);
+                        for (int d2 = 0; d2 < 3; ++d2)
+                            if (d2 != d) q *= f[d2];
+                        g[d] = q;
+                    }
+                    const int node = (kx + (l & 1)) + M.NX * ((ky + ((l >> 1) & 1)) + M.NY * (kz + (l >> 2)));
+                    const double ux = F[((size_t)node * 3 + 0) * ld + col];
+                    const double uy = F[((size_t)node * 3 + 1) * ld + col];
+                    const double uz = F[((size_t)node * 3 + 2) * ld + col];
+                    eps[0] += g[0] * ux;
+                    eps[1] += g[1] * uy;
+                    eps[2] += g[2] * uz;
+                    eps[3] += g[1] * ux + g[0] * uy;
+                    eps[4] += g[2] * uy + g[1] * uz;
+                    eps[5] += g[2] * ux + g[0] * uz;
+                }
+                const int e = kx + M.ex * (ky + M.ey * kz);
+                const int k = mat[e];
+                const double lam = mt.lam[k], mu = mt.mu[k], th = (col == m) ? mt.tm[k] : 0.0;
+                const double tr = eps[0] + eps[1] + eps[2];
+                sig[0] += w * (lam * tr + 2 * mu * eps[0] - th);
+                sig[1] += w * (lam * tr + 2 * mu * eps[1] - th);
+                sig[2] += w * (lam * tr + 2 * mu * eps[2] - th);
+                sig[3] += w * (mu * eps[3]);
+                sig[4] += w * (mu * eps[4]);
+                sig[5] += w * (mu * eps[5]);
+            }
+    for (int r = 0; r < 6; ++r) Sg[((size_t)p * 6 + r) * ld + col] = sig[r];
+}
+
 // Gauss mean of imported stress modes.
 __global__ void k_smean(int n_el, int m1, int ld, const double* S, double* Smean) {
     size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -506,6 +600,31 @@ __global__ void k_smean(int n_el, int m1, int ld, const double* S, double* Smean
 }
 
 }  // namespace
+
+void build_grid_modes(mstress_block blk, int side) {
+    MS_REQUIRE(side >= 1 && side <= 400, MSTRESS_EINVAL, "grid side must be in [1, 400]");
+    MS_REQUIRE(blk->has_mat && blk->has_F, MSTRESS_EINVAL,
+               "gridded output needs a block built by mstress_build_block (materials and basis on the device)");
+    if (blk->grid_side == side) return;
+    for (auto& d : blk->Sgrid_lp) d.reset();
+    for (auto& d : blk->Sgrid_tc) d.reset();
+    const int n_grid = side * side;
+    alloc_into(blk->ctx, blk->Sgrid, (size_t)6 * n_grid * blk->ld * sizeof(double));
+    MatTab mt;
+    std::memset(&mt, 0, sizeof(mt));
+    for (int k = 0; k < kMaxMat; ++k) {
+        mt.lam[k] = blk->mat_lam[k];
+        mt.mu[k] = blk->mat_mu[k];
+        mt.tm[k] = blk->mat_tm[k];
+    }
+    Mesh M{blk->ex, blk->ey, blk->ez, blk->ex + 1, blk->ey + 1, blk->ez + 1, blk->n_nodes, 0};
+    k_grid_modes<<<dim3(n_grid, (blk->m1 + 31) / 32), 32, 0, blk->ctx->stream>>>(
+        M, blk->mat_id.as<uint8_t>(), mt, blk->m, blk->ld, blk->F.as<double>(), side, blk->lx, blk->ly, blk->lz,
+        blk->Sgrid.as<double>());
+    MS_LAUNCH_CHECK();
+    blk->grid_side = side;
+    blk->n_grid = n_grid;
+}
 
 void block_compute_smean(mstress_block blk) {
     size_t n = (size_t)blk->n_el * 6 * blk->m1;
@@ -698,6 +817,13 @@ int build_block(mstress_ctx ctx, const mstress_block_mesh* mesh, const mstress_t
     MS_CUDA(cudaMemcpy2DAsync(B.F.ptr, ld * sizeof(double), U0.ptr, NCP * sizeof(double), m1 * sizeof(double),
                               B.n_dof, cudaMemcpyDeviceToDevice, st));
     B.has_F = true;
+    B.mat_id = std::move(d_mat);   // kept for point evaluations (gridded output)
+    for (int k = 0; k < kMaxMat; ++k) {
+        B.mat_lam[k] = mt.lam[k];
+        B.mat_mu[k] = mt.mu[k];
+        B.mat_tm[k] = mt.tm[k];
+    }
+    B.has_mat = true;
     MS_CUDA(cudaStreamSynchronize(st));
     *out = blk.release();
     if (status != MSTRESS_OK)

@@ -184,7 +184,7 @@ __device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev
                     if (use) {
                         const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
                         if (sidx >= 0)
-                            s[u] += (V)Y[(A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp];
+                            s[u] += (V)__ldcg(Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp);
                     }
                 }
             }
@@ -250,7 +250,7 @@ __device__ __forceinline__ void isum_update_item(const VecWork& it, const ArrayD
                     const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
                     if (use) {
                         const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
-                        if (sidx >= 0) s[u] += Y[(A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp];
+                        if (sidx >= 0) s[u] += __ldcg(Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp);
                     }
                 }
             }
@@ -331,7 +331,7 @@ __device__ __forceinline__ void resident_update_item(long long start, int count,
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int off = soff[c * stride + l];
-                    if (off >= 0) s[u] += Y[off];
+                    if (off >= 0) s[u] += __ldcg(Y + off);
                 }
             }
         }

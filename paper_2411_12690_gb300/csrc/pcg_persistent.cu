@@ -68,11 +68,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // CTA 0 accumulates the wall time of a phase (from its start to the end of
-// the grid barrier that closes it) into timers[phase].
-__device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned long long& t_prev) {
+// the grid barrier that closes it) in registers (acc[phase]); they are added
+// to timers[] once, when the kernel ends, so that no global memory round trip
+// joins the iteration's critical path.
+__device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned long long& t_prev,
+                                           unsigned long long (&acc)[4]) {
     if (a.timers && blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long t = global_ns();
-        a.timers[phase] += t - t_prev;
+        acc[phase] += t - t_prev;
         t_prev = t;
     }
 }
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     }
     __syncthreads();
     unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
+    unsigned long long t_acc[4] = {0, 0, 0, 0};
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
         bool failed = false;
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             atomicExch(a.abort, 1);
         }
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
-        phase_mark(a, 0, t_prev);
+        phase_mark(a, 0, t_prev, t_acc);
         if constexpr (FUSED) {
             // ---- alpha from the group sums of p_e^T Y_e (one array: every CTA folds)
             if (solo && s_active) {
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             if (!solo) switch_array(cur, -1, 1);
         }
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
-        phase_mark(a, 1, t_prev);
+        phase_mark(a, 1, t_prev, t_acc);
         if (solo && s_active) {
             const double pq = pi::cta_fold8(a.part_pq + s_A.vwork_off, s_A.n_vwork, sh8);
             if (tid == 0) {
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         }
         }   // three-phase iteration
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
-        phase_mark(a, FUSED ? 1 : 2, t_prev);
+        phase_mark(a, FUSED ? 1 : 2, t_prev, t_acc);
         if (solo && s_active) {
             double rz, rr;
             pi::cta_fold8_2(a.part_rz + s_A.vwork_off, a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8, rz, rr);
@@ -510,9 +514,11 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             }
             __syncthreads();
         }
-        if (a.timers && blockIdx.x == 0 && tid == 0) a.timers[3] += 1;
+        if (a.timers && blockIdx.x == 0 && tid == 0) t_acc[3] += 1;
         if (solo ? !s_active : *(volatile int*)a.n_active <= 0) break;
     }
+    if (a.timers && blockIdx.x == 0 && tid == 0)
+        for (int k = 0; k < 4; ++k) a.timers[k] += t_acc[k];
     if constexpr (FUSED) {
         if (resident && (int)blockIdx.x < a.n_vwork) {   // the slice's x and r back to global memory
             __syncthreads();

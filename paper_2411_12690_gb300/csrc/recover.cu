@@ -211,6 +211,22 @@ void ensure_lowp(mstress_block blk, int precision) {
                    precision);
 }
 
+static void ensure_grid_lowp(mstress_block blk, int precision) {
+    if (!blk->Sgrid_lp[precision].ptr)
+        round_rows(blk->ctx, blk->Sgrid_lp[precision], blk->Sgrid.as<double>(), (long long)6 * blk->n_grid, blk->m1,
+                   blk->ld, precision);
+}
+
+// Grid points per block of a solution's gridded output (every block model of
+// the solve must carry the same grid).
+static int grid_points(const mstress_sol_s* s) {
+    const int side = s->types[0]->grid_side;
+    MS_REQUIRE(side > 0, MSTRESS_EINVAL, "no grid modes: call mstress_block_grid on the solution's block models");
+    for (auto b : s->types)
+        MS_REQUIRE(b->grid_side == side, MSTRESS_EINVAL, "the block models of a solve carry different grids");
+    return side * side;
+}
+
 static void ensure_S_lowp(mstress_block blk, int precision) {
     if (!blk->S_lp[precision].ptr)
         round_rows(blk->ctx, blk->S_lp[precision], blk->S.as<double>(), (long long)48 * blk->n_el, blk->m1, blk->ld,
@@ -225,6 +241,7 @@ size_t recover_bytes(const mstress_sol_s* s, int what) {
         case MSTRESS_SIGMA_GP: return (size_t)s->n_blocks * s->n_el * 48 * w;
         case MSTRESS_U_NODE: return (size_t)s->n_blocks * s->n_dof_block * sizeof(double);
         case MSTRESS_LATTICE: return (size_t)s->n_vec * sizeof(double);
+        case MSTRESS_VM_GRID: return (size_t)s->n_blocks * grid_points(s) * w;
         default: throw Error{MSTRESS_EINVAL, "unknown recovery output"};
     }
 }
@@ -279,9 +296,9 @@ void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev) {
     }
     if (what == MSTRESS_LATTICE) {
         MS_CUDA(cudaMemcpyAsync(out, s->v64.x.ptr, bytes, cudaMemcpyDeviceToDevice, st));
-    } else if (what == MSTRESS_VM_ELEM && s->precision != MSTRESS_FP64 &&
+    } else if ((what == MSTRESS_VM_ELEM || what == MSTRESS_VM_GRID) && s->precision != MSTRESS_FP64 &&
                tc_recover_supported(s->types[0]->m1, s->precision)) {
-        recover_vm_tc(s, static_cast<float*>(out));
+        recover_vm_tc(s, static_cast<float*>(out), what == MSTRESS_VM_GRID);
     } else if (what == MSTRESS_COEFF) {
         long long n = s->n_blocks * s->m;
         k_coeff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->n_blocks, s->d_bref.as<BlockRef>(),
@@ -303,20 +320,26 @@ void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev) {
         mstress_block t0 = s->types[0];
         a.m1 = t0->m1;
         a.ld = t0->ld;
-        a.n_el = s->n_el;
+        const bool grid = what == MSTRESS_VM_GRID;
+        a.n_el = grid ? grid_points(s) : s->n_el;
         a.x = s->v64.x.as<double>();
         a.out = out;
-        a.vm = what == MSTRESS_VM_ELEM;
-        if (what == MSTRESS_VM_ELEM) a.n_rows = 6 * s->n_el;
+        a.vm = what == MSTRESS_VM_ELEM || grid;
+        if (a.vm) a.n_rows = 6 * a.n_el;
         else if (what == MSTRESS_SIGMA_GP) a.n_rows = 48 * s->n_el;
         else a.n_rows = s->n_dof_block;
-        a.out_ld = a.vm ? s->n_el : a.n_rows;
+        a.out_ld = a.vm ? a.n_el : a.n_rows;
         a.plane = (long long)a.n_rows * a.ld;
         for (int t = 0; t < s->n_types; ++t) {
             mstress_block b = s->types[t];
             if (what == MSTRESS_U_NODE) {
                 MS_REQUIRE(b->has_F, MSTRESS_EINVAL, "a block model holds no basis F (imported without it)");
                 a.rows[t] = b->F.ptr;
+            } else if (grid && mode == MSTRESS_FP64) {
+                a.rows[t] = b->Sgrid.ptr;
+            } else if (grid) {
+                ensure_grid_lowp(b, mode);
+                a.rows[t] = b->Sgrid_lp[mode].ptr;
             } else if (mode == MSTRESS_FP64) {
                 a.rows[t] = what == MSTRESS_VM_ELEM ? b->Smean.ptr : b->S.ptr;
             } else if (what == MSTRESS_VM_ELEM) {

@@ -203,7 +203,8 @@ void build_tc_operator(mstress_block blk, int prec);   // K_r image for the tens
 
 // tensor-core von Mises recovery (tc_recover.cu)
 bool tc_recover_supported(int m1, int prec);
-void recover_vm_tc(mstress_sol_s* s, float* out);
+// (grid: the cut-plane grid modes instead of the Gauss-mean stress modes)
+void recover_vm_tc(mstress_sol_s* s, float* out, bool grid = false);
 
 // recovery (recover.cu)
 void recover(mstress_sol_s* s, int what, void* dst, bool dst_dev);

@@ -659,44 +659,47 @@ bool tc_recover_supported(int m1, int prec) {
     return prec != MSTRESS_FP64 && (rec_shape(m1, 1, prec).stages >= 1 || recs_shape(m1, 1, prec).stages >= 2);
 }
 
-void build_tc_smean(mstress_block blk, int prec) {
-    if (blk->Smean_tc[prec].ptr) return;
-    if (rec_shape(blk->m1, blk->n_el, prec).stages < 1) {   // streamed layout, slot by slot
-        RecsShape sh = recs_shape(blk->m1, blk->n_el, prec);
-        alloc_into(blk->ctx, blk->Smean_tc[prec], (size_t)sh.n_etiles * sh.nks * sh.slot, true);
+// Tensor-core image of a block's von Mises mode matrix: the Gauss-mean
+// stress modes (per-element output) or, with grid, the cut-plane grid modes.
+void build_tc_smean(mstress_block blk, int prec, bool grid) {
+    ms::DBuf& img = grid ? blk->Sgrid_tc[prec] : blk->Smean_tc[prec];
+    if (img.ptr) return;
+    const int n_pts = grid ? blk->n_grid : blk->n_el;
+    const double* Sm = grid ? blk->Sgrid.as<double>() : blk->Smean.as<double>();
+    cudaStream_t st = blk->ctx->stream;
+    if (rec_shape(blk->m1, n_pts, prec).stages < 1) {   // streamed layout, slot by slot
+        RecsShape sh = recs_shape(blk->m1, n_pts, prec);
+        alloc_into(blk->ctx, img, (size_t)sh.n_etiles * sh.nks * sh.slot, true);
         const long long n = (long long)sh.n_etiles * 128 * sh.kpad;
         const unsigned g = (unsigned)((n + 255) / 256);
-        const double* Sm = blk->Smean.as<double>();
-        uint8_t* out = blk->Smean_tc[prec].as<uint8_t>();
-        cudaStream_t st = blk->ctx->stream;
+        uint8_t* out = img.as<uint8_t>();
         switch (prec) {
-            case MSTRESS_TF32: k_smean_image_s<MSTRESS_TF32><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, blk->n_el, sh, out); break;
-            case MSTRESS_BF16: k_smean_image_s<MSTRESS_BF16><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, blk->n_el, sh, out); break;
-            default: k_smean_image_s<MSTRESS_BF16X3><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, blk->n_el, sh, out); break;
+            case MSTRESS_TF32: k_smean_image_s<MSTRESS_TF32><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, n_pts, sh, out); break;
+            case MSTRESS_BF16: k_smean_image_s<MSTRESS_BF16><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, n_pts, sh, out); break;
+            default: k_smean_image_s<MSTRESS_BF16X3><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, n_pts, sh, out); break;
         }
         MS_LAUNCH_CHECK();
         return;
     }
-    RecShape sh = rec_shape(blk->m1, blk->n_el, prec);
-    alloc_into(blk->ctx, blk->Smean_tc[prec], (size_t)sh.n_etiles * sh.set, true);
+    RecShape sh = rec_shape(blk->m1, n_pts, prec);
+    alloc_into(blk->ctx, img, (size_t)sh.n_etiles * sh.set, true);
     const long long n = (long long)sh.n_etiles * 128 * sh.kpad;
     const unsigned g = (unsigned)((n + 255) / 256);
-    const double* Sm = blk->Smean.as<double>();
-    uint8_t* out = blk->Smean_tc[prec].as<uint8_t>();
-    cudaStream_t st = blk->ctx->stream;
+    uint8_t* out = img.as<uint8_t>();
     switch (prec) {
-        case MSTRESS_TF32: k_smean_image<MSTRESS_TF32><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, blk->n_el, sh, out); break;
-        case MSTRESS_BF16: k_smean_image<MSTRESS_BF16><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, blk->n_el, sh, out); break;
-        default: k_smean_image<MSTRESS_BF16X3><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, blk->n_el, sh, out); break;
+        case MSTRESS_TF32: k_smean_image<MSTRESS_TF32><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, n_pts, sh, out); break;
+        case MSTRESS_BF16: k_smean_image<MSTRESS_BF16><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, n_pts, sh, out); break;
+        default: k_smean_image<MSTRESS_BF16X3><<<g, 256, 0, st>>>(Sm, blk->ld, blk->m1, n_pts, sh, out); break;
     }
     MS_LAUNCH_CHECK();
 }
 
 // Streamed variant of recover_vm_tc for large bases.
-void recover_vm_tcs(mstress_sol_s* s, float* out) {
+void recover_vm_tcs(mstress_sol_s* s, float* out, bool grid) {
     mstress_ctx ctx = s->ctx;
     const int prec = s->precision;
-    RecsShape sh = recs_shape(s->types[0]->m1, s->n_el, prec);
+    const int n_pts = grid ? s->types[0]->n_grid : s->n_el;
+    RecsShape sh = recs_shape(s->types[0]->m1, n_pts, prec);
     MS_REQUIRE(sh.stages >= 2, MSTRESS_EINVAL, "basis too large for the streamed recovery");
     const size_t cbytes = (size_t)s->n_awork_rec * sh.nks * sh.slot;
     if (s->cimg.bytes < cbytes) alloc_into(ctx, s->cimg, cbytes, false);
@@ -718,38 +721,40 @@ void recover_vm_tcs(mstress_sol_s* s, float* out) {
     ra.blist = s->d_blist.as<int>();
     ra.cimg = cimg;
     for (int t = 0; t < s->n_types; ++t) {
-        build_tc_smean(s->types[t], prec);
-        ra.simg[t] = s->types[t]->Smean_tc[prec].as<uint8_t>();
+        build_tc_smean(s->types[t], prec, grid);
+        ra.simg[t] = (grid ? s->types[t]->Sgrid_tc[prec] : s->types[t]->Smean_tc[prec]).as<uint8_t>();
     }
-    ra.n_el = s->n_el;
+    ra.n_el = n_pts;
     ra.out = out;
     ra.err = s->flag.as<int>() + 2;
     const long long pairs = (long long)s->n_awork_rec * sh.n_etiles;
-    const int grid = (int)std::max(1LL, std::min(pairs, (long long)ctx->num_sms));
+    const int ncta = (int)std::max(1LL, std::min(pairs, (long long)ctx->num_sms));
     // about eight units per CTA at least, so that the last round is nearly full
     ra.n_seg = (int)std::max(1LL, std::min((long long)sh.n_etiles,
-                                           (8LL * grid + s->n_awork_rec - 1) / std::max(1, s->n_awork_rec)));
+                                           (8LL * ncta + s->n_awork_rec - 1) / std::max(1, s->n_awork_rec)));
     switch (prec) {
-        case MSTRESS_TF32: k_recover_tcs<MSTRESS_TF32><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
-        case MSTRESS_BF16: k_recover_tcs<MSTRESS_BF16><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
-        default: k_recover_tcs<MSTRESS_BF16X3><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        case MSTRESS_TF32: k_recover_tcs<MSTRESS_TF32><<<ncta, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        case MSTRESS_BF16: k_recover_tcs<MSTRESS_BF16><<<ncta, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        default: k_recover_tcs<MSTRESS_BF16X3><<<ncta, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
     }
     MS_LAUNCH_CHECK();
 }
 
-// Von Mises of every element of every block into out (FP32, [block][n_el]).
-void recover_vm_tc(mstress_sol_s* s, float* out) {
+// Von Mises of every element of every block into out (FP32, [block][n_el]),
+// or, with grid, of every cut-plane grid point ([block][n_grid]).
+void recover_vm_tc(mstress_sol_s* s, float* out, bool grid) {
     mstress_ctx ctx = s->ctx;
     const int prec = s->precision;
     mstress_block t0 = s->types[0];
-    RecShape sh = rec_shape(t0->m1, s->n_el, prec);
+    const int n_pts = grid ? t0->n_grid : s->n_el;
+    RecShape sh = rec_shape(t0->m1, n_pts, prec);
     static bool configured = false;
     if (!configured) {
         configure_tc_recover_kernels();
         configured = true;
     }
     if (sh.stages < 1) {
-        recover_vm_tcs(s, out);
+        recover_vm_tcs(s, out, grid);
         return;
     }
     const size_t cbytes = (size_t)s->n_awork_rec * sh.set;
@@ -774,18 +779,18 @@ void recover_vm_tc(mstress_sol_s* s, float* out) {
     ra.blist = s->d_blist.as<int>();
     ra.cimg = cimg;
     for (int t = 0; t < s->n_types; ++t) {
-        build_tc_smean(s->types[t], prec);
-        ra.simg[t] = s->types[t]->Smean_tc[prec].as<uint8_t>();
+        build_tc_smean(s->types[t], prec, grid);
+        ra.simg[t] = (grid ? s->types[t]->Sgrid_tc[prec] : s->types[t]->Smean_tc[prec]).as<uint8_t>();
     }
-    ra.n_el = s->n_el;
+    ra.n_el = n_pts;
     ra.out = out;
     ra.err = s->flag.as<int>() + 2;
     const long long pairs = (long long)s->n_awork_rec * sh.n_etiles;
-    const int grid = (int)std::max(1LL, std::min(pairs, (long long)ctx->num_sms));
+    const int ncta = (int)std::max(1LL, std::min(pairs, (long long)ctx->num_sms));
     switch (prec) {
-        case MSTRESS_TF32: k_recover_tc<MSTRESS_TF32><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
-        case MSTRESS_BF16: k_recover_tc<MSTRESS_BF16><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
-        default: k_recover_tc<MSTRESS_BF16X3><<<grid, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        case MSTRESS_TF32: k_recover_tc<MSTRESS_TF32><<<ncta, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        case MSTRESS_BF16: k_recover_tc<MSTRESS_BF16><<<ncta, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
+        default: k_recover_tc<MSTRESS_BF16X3><<<ncta, kRecsThreads, sh.smem, ctx->stream>>>(ra, sh); break;
     }
     MS_LAUNCH_CHECK();
 }

@@ -1,7 +1,8 @@
 """The reduced-precision operator of the inner PCG (Eq. 18 applied matrix-free,
 with the interface sum of section 4.3) at every basis size the tensor cores
-take: m = 78 (operator resident in shared memory), m = 168 and m = 294
-(operator streamed along K, the latter split into two MMA column groups).
+take: m = 78 (operator resident in shared memory), m = 168, m = 294 and
+m = 456 (operator streamed along K, the last two split into two MMA column
+groups).
 
 Bound, per lattice DOF g of y = A_global x with x rounded to FP32: each element
 product entry is a K-term dot product of operands rounded to the mode's format
@@ -27,7 +28,8 @@ U_IN = {L.MSTRESS_TF32: 2.0 ** -11, L.MSTRESS_BF16: 2.0 ** -8, L.MSTRESS_BF16X3:
 MODES = [L.MSTRESS_TF32, L.MSTRESS_BF16, L.MSTRESS_BF16X3]
 SPECS = {2: W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, 2),    # m = 78
          3: W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, 3),    # m = 168
-         4: W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, 4)}    # m = 294
+         4: W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, 4),    # m = 294
+         5: W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, 5)}    # m = 456
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +45,7 @@ def _abs_operator(blocks, site_type):
     return A, lat, shape
 
 
-@pytest.mark.parametrize("order", [2, 3, 4])
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
 @pytest.mark.parametrize("mode", MODES)
 def test_reduced_operator_within_rounding_bound(api, order, mode):
     import torch
@@ -74,11 +76,11 @@ def test_reduced_operator_within_rounding_bound(api, order, mode):
     assert np.all(y[holes] == 0.0)
 
 
-@pytest.mark.parametrize("mode", MODES)
-def test_refinement_m294_reaches_fp64_accuracy(api, mode):
+@pytest.mark.parametrize("order,mode", [(4, m) for m in MODES] + [(5, L.MSTRESS_BF16X3), (5, L.MSTRESS_TF32)])
+def test_refinement_streamed_reaches_fp64_accuracy(api, order, mode):
     """Iterative refinement around the streamed tensor-core operator reaches
-    the FP64 path's accuracy on the element DOFs."""
-    spec = SPECS[4]
+    the FP64 path's accuracy on the element DOFs (m = 294 and 456)."""
+    spec = SPECS[order]
     ctx = api.Context(precision=mode)
     blks = [ctx.build_block(spec), ctx.build_block(spec.dummy())]
     st = W.site_types(9, 8, 0.8, seed=5)
@@ -91,7 +93,7 @@ def test_refinement_m294_reaches_fp64_accuracy(api, mode):
     assert info["status"] == 0 and info["rel_res"] <= 1e-12
     assert rel_l2(c, osol.coeffs) <= 1e-9
     # per-element von Mises through the tensor-core recovery with K streamed
-    # (m + 1 = 295 in the split modes), within its rounding bound
+    # (m + 1 = 295 or 457), within its rounding bound
     from test_gpu_mixed import vm_bound
     vm = sol.recover(L.MSTRESS_VM_ELEM).reshape(-1, spec.ex * spec.ey * spec.ez)
     ovm = mor.recover_vm(ob, osol)

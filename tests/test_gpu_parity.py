@@ -48,7 +48,7 @@ def test_local_stage_matches_oracle(small_blocks):
         _check_block(blk, ob)
 
 
-@pytest.mark.parametrize("order", [1, 3, 4])
+@pytest.mark.parametrize("order", [1, 3, 4, 5])
 def test_local_stage_other_orders(ctx, order):
     spec = W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, order)
     _check_block(ctx.build_block(spec), oracle_block(spec))

@@ -1,0 +1,79 @@
+"""Scenario 1 of section 5.1: stand-alone TSV arrays with the top and the
+bottom face clamped, and the convergence study of Table 3 over the face
+basis order, run through the GPU local stage.
+
+* convergence: blocks of orders 1 to 5 (m = 24, 78, 168, 294, 456) built on
+  the GPU, a 2x2 array solved in FP64 with both faces clamped; the
+  normalised MAE of the gridded mid-plane von Mises against O-FEM (the error
+  measure of section 5.1) falls at every step of the order, and every solve
+  matches the oracle's reduced model (element DOFs at rel. L2 1e-9);
+* the paper's block (pitch 15 um and 10 um, (4,4,4) nodes, m = 168), both
+  faces clamped, in the mixed mode the benchmark sweeps: element DOFs at
+  1e-9 of the oracle and every sampled von Mises value within its bound.
+"""
+import numpy as np
+import pytest
+
+from cases import oracle_pair, oracle_solve, oracle_vm_rows, rel_l2, vm_bound_rows
+from oracle import fem, mor
+from paper_2411_12690_gb300 import _lib as L
+from paper_2411_12690_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+DT = W.DT_DEFAULT
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2411_12690_gb300 import api, build
+    build.build()
+    return api
+
+
+def test_convergence_over_orders_top_bottom_clamped(api):
+    base = W.BLOCK_SMALL
+    st = np.array([[0, 0], [1, 0]], dtype=np.uint8)
+    side = 20
+    t_mesh = fem.tsv_block_mesh(base.lx, base.ly, base.lz, base.ex, base.ey, base.ez, base.r_cu, base.t_liner)
+    d_mesh = fem.tsv_block_mesh(base.lx, base.ly, base.lz, base.ex, base.ey, base.ez, 0.0, 0.0)
+    amesh, u_fem, _ = fem.solve_array_fem(t_mesh, [t_mesh.mat_id, d_mesh.mat_id], st, DT, clamp_top=True)
+    ref = fem.array_grid_vm(amesh, u_fem, DT, 2, 2, base.lx, base.ly, side)
+    ctx = api.Context()
+    errs = []
+    for order in (1, 2, 3, 4, 5):
+        spec = W.BlockSpec(base.lx, base.ly, base.lz, base.ex, base.ey, base.ez, base.r_cu, base.t_liner, order)
+        blks = [ctx.build_block(spec).grid(side), ctx.build_block(spec.dummy()).grid(side)]
+        sol = ctx.solve(st, blks, DT, clamp_top=True)
+        assert sol.info()["status"] == 0
+        _, osol = oracle_solve(spec, st, DT, clamp_top=True)
+        c = sol.recover(L.MSTRESS_COEFF).reshape(osol.coeffs.shape)
+        assert rel_l2(c, osol.coeffs) <= 1e-9
+        vm = sol.recover(L.MSTRESS_VM_GRID).reshape(4, side * side)
+        errs.append(fem.normalized_mae(vm, ref))
+        for b in blks:
+            b.close()
+    print("normalised MAE vs O-FEM by order 1..5 (m = 24, 78, 168, 294, 456):", ["%.3f%%" % (100 * e) for e in errs])
+    assert all(errs[k] > errs[k + 1] for k in range(4))
+
+
+@pytest.mark.parametrize("spec", [W.BLOCK_P15_O3, W.BLOCK_P10_O3])
+def test_paper_block_top_bottom_clamped_mixed(api, spec):
+    ctx = api.Context(precision=L.MSTRESS_BF16X3)
+    blks = [ctx.build_block(spec), ctx.build_block(spec.dummy())]
+    st = W.site_types(10, 10, 1.0)
+    sol = ctx.solve(st, blks, DT, clamp_top=True)
+    info = sol.info()
+    assert info["status"] == 0 and info["rel_res"] <= 1e-12
+    ob, osol = oracle_solve(spec, st, DT, clamp_top=True)
+    c = sol.recover(L.MSTRESS_COEFF).reshape(osol.coeffs.shape)
+    assert rel_l2(c, osol.coeffs) <= 1e-9
+    n_el = spec.ex * spec.ey * spec.ez
+    vm = sol.recover(L.MSTRESS_VM_ELEM).reshape(st.size, n_el).astype(np.float64)
+    pick = np.array([0, 9, 45, 54, 90, 99])
+    types = st.ravel()[pick]
+    ovm = oracle_vm_rows(ob, types, osol.coeffs[pick], DT)
+    bound = vm_bound_rows(ob, types, osol.coeffs[pick], DT, L.MSTRESS_BF16X3)
+    err = np.abs(vm[pick] - ovm)
+    print(f"p={spec.lx} m={ob[0].m}: iters {info['iters']} outer {info['outer']}, vm rel L2 "
+          f"{rel_l2(vm[pick], ovm):.2e}, max err/bound {np.max(err / bound):.3f}")
+    assert np.all(err <= bound + 1e-12 * ovm.max())

@@ -325,3 +325,16 @@ def test_gridded_error_falls_with_the_basis_order():
     print("normalised MAE by order 1, 2, 4:", errs)
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.02
+
+
+def test_grid_stress_modes_are_the_pointwise_stress_of_each_basis_column(small_block):
+    """Linearity of Eqs. 15 and 1: the grid modes times [c; dT] give the
+    point stresses of the fine field F [c; dT] under dT."""
+    rng = np.random.default_rng(9)
+    c = rng.standard_normal(small_block.m) * 1e-3
+    modes = mor.grid_stress_modes(small_block, 7)
+    u = mor.block_displacement(small_block, c, -250.0)
+    m = small_block.mesh
+    ref = fem.point_stresses(m, u, -250.0, fem.midplane_grid(m.lx, m.ly, m.lz, 7))
+    got = modes @ np.concatenate([c, [-250.0]])
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
