@@ -456,7 +456,139 @@ def extra_records(args, local):
         t0 = time.perf_counter()
         recs[f"serve_{prec_name}"] = dict(serve_run(prec_name, nreq, args.load, local),
                                           wall_s=time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    recs["scenario1_sweep_bf16x3"] = dict(scenario1_run("bf16x3", local), wall_s=time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    recs["submodel_bf16x3"] = dict(submodel_run("bf16x3", local), wall_s=time.perf_counter() - t0)
     return recs
+
+
+# the paper's global-stage times (seconds) for scenario 1 (Table 1) and the
+# sub-model of scenario 2 (Table 2), on its CPU (context for the GPU times)
+PAPER_S1_SECONDS = {15: {10: 2.5, 20: 4.4, 30: 9.5, 40: 13.1, 50: 17.1},
+                    10: {10: 2.3, 20: 4.5, 30: 11.4, 40: 13.9, 50: 18.5}}
+PAPER_S2_SECONDS = (3.5, 3.7)
+
+
+def _timed_steps(stream, step, steps, warmup):
+    """Device time (CUDA events on the context stream) of `steps` calls of
+    step() after `warmup` untimed ones; returns seconds per step."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1) / 1e3
+    return tot / steps
+
+
+def scenario1_run(prec_name, local, sizes=(10, 20, 30, 40, 50), steps=3, warmup=1):
+    """Scenario 1 of section 5.1: stand-alone arrays of 10x10 .. 50x50 TSV
+    blocks, pitch 15 and 10 um, (4,4,4) interpolation nodes (m = 168), top and
+    bottom clamped, dT = -250 K; a step is the solve plus the per-element von
+    Mises and the gridded half-height von Mises (100 x 100 points per block,
+    the paper's error-measure output)."""
+    import torch
+
+    from paper_2411_12690_gb300 import _lib as L
+    from paper_2411_12690_gb300 import api
+    from paper_2411_12690_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(stream=stream.cuda_stream, precision=PREC[prec_name])
+    out = {"metric": "TSV blocks solved+recovered/s per array size (scenario 1)", "unit": "blocks/s",
+           "dtype": DTYPE[prec_name], "steps": steps, "warmup": warmup, "by_pitch": {}}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for pitch, spec in ((15, W.BLOCK_P15_O3), (10, W.BLOCK_P10_O3)):
+        blks = [ctx.build_block(spec).grid(100), ctx.build_block(spec.dummy()).grid(100)]
+        n_el = spec.ex * spec.ey * spec.ez
+        rows = {}
+        for n in sizes:
+            st = W.site_types(n, n, 1.0)
+            vm = torch.empty(n * n * n_el, dtype=torch.float32, device="cuda")
+            vg = torch.empty(n * n * 10000, dtype=torch.float32, device="cuda")
+            info = {}
+
+            def step():
+                sol = ctx.solve(st, blks, W.DT_DEFAULT, clamp_top=True)
+                sol.recover(L.MSTRESS_VM_ELEM, out=vm)
+                sol.recover(L.MSTRESS_VM_GRID, out=vg)
+                info.update(sol.info())
+                sol.close()
+
+            sec = _timed_steps(stream, step, steps, warmup)
+            rows[f"{n}x{n}"] = {"blocks": n * n, "ms_per_step": 1e3 * sec, "value": n * n / sec,
+                                "pcg_iters": info["iters"], "refinement_steps": info["outer"],
+                                "rel_res": info["rel_res"],
+                                "paper_global_stage_s": PAPER_S1_SECONDS[pitch][n],
+                                "paper_over_this": PAPER_S1_SECONDS[pitch][n] / sec}
+            del vm, vg
+        out["by_pitch"][f"p{pitch}"] = rows
+        for b in blks:
+            b.close()
+    out["clocks"] = clocks.stop()
+    out["config"] = {"workload": "stand-alone TSV arrays, p = 15 um (24x24x20 mesh) and 10 um (16x16x20 mesh) "
+                                 "blocks, (4,4,4) nodes (m=168), top+bottom clamped, dT=-250 K; solve + per-element "
+                                 "and gridded (100x100 per block) von Mises",
+                     "paper_times": "the paper's global-stage seconds on its CPU (8 threads), context only"}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def submodel_run(prec_name, local, steps=5, warmup=2):
+    """Scenario 2 (sections 4.4, 5.1): a 15x15 TSV array of pitch-15 um
+    blocks ((4,4,4) nodes) inside two rings of dummy blocks, every outer face
+    of the sub-model driven by the synthetic coarse-model boundary field
+    (lifting), no clamped face; solve + gridded von Mises (100 x 100 per
+    block)."""
+    import torch
+
+    from paper_2411_12690_gb300 import _lib as L
+    from paper_2411_12690_gb300 import api
+    from paper_2411_12690_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(stream=stream.cuda_stream, precision=PREC[prec_name])
+    spec = W.BLOCK_P15_O3
+    blks = [ctx.build_block(spec).grid(100), ctx.build_block(spec.dummy()).grid(100)]
+    st = W.submodel_sites(15, 2)
+    ny, nx = st.shape
+    dof, val = W.submodel_boundary(nx, ny, spec, seed=0)
+    presc = dict(zip(dof.tolist(), val.tolist()))
+    vg = torch.empty(st.size * 10000, dtype=torch.float32, device="cuda")
+    info = {}
+
+    def step():
+        sol = ctx.solve(st, blks, W.DT_DEFAULT, clamp_bottom=False, prescribed=presc)
+        sol.recover(L.MSTRESS_VM_GRID, out=vg)
+        info.update(sol.info())
+        sol.close()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    sec = _timed_steps(stream, step, steps, warmup)
+    clk = clocks.stop()
+    ctx.close()
+    torch.cuda.empty_cache()
+    return {"metric": "sub-model blocks solved+recovered/s (15x15 TSV array + 2 dummy rings)", "unit": "blocks/s",
+            "value": st.size / sec, "ms_per_step": 1e3 * sec, "steps": steps, "warmup": warmup,
+            "dtype": DTYPE[prec_name], "pcg_iters": info["iters"], "refinement_steps": info["outer"],
+            "rel_res": info["rel_res"], "paper_global_stage_s": list(PAPER_S2_SECONDS),
+            "config": {"workload": "19x19 sites (15x15 TSV + 2 dummy rings), p = 15 um, (4,4,4) nodes (m=168), "
+                                   "synthetic warpage-like boundary field on all six faces by lifting, dT=-250 K; "
+                                   "solve + gridded von Mises (100x100 per block)",
+                       "prescribed_dofs": int(dof.size)},
+            "clocks": clk}
 
 
 def _variant_models(ctx, W):

@@ -298,6 +298,15 @@ int mstress_server_result(mstress_server srv, int64_t id, void* dst, size_t dst_
 int mstress_server_release(mstress_server srv, int64_t id);
 void mstress_free_server(mstress_server srv);
 
+/* Bounded device waits. A grid-barrier wait of the persistent solver gives up
+   after limit_ns nanoseconds of device time (default 2e9): the kernel records
+   the failure, every CTA leaves, and the solve returns
+   MSTRESS_EDEVICE_TIMEOUT; the context stays usable. withhold_next = 1 makes
+   the next persistent solver launch on this context skip one CTA's first
+   barrier arrival, once, so that the wait runs out: a test hook for the
+   timeout path (no fault, no trap; every wait stays bounded). */
+int mstress_set_wait_limit(mstress_ctx ctx, int64_t limit_ns, int withhold_next);
+
 /* Number of CUDA kernels this library has launched in this process (a graph
    replay counts its kernel nodes). For accounting in benchmarks. */
 int mstress_launch_count(int64_t* n);

@@ -111,6 +111,7 @@ SIGNATURES = {
     "mstress_free_sol": (None, [P]),
     "mstress_apply": (I, [P, C.POINTER(mstress_layout), P, P, I]),
     "mstress_launch_count": (I, [C.POINTER(C.c_int64)]),
+    "mstress_set_wait_limit": (I, [P, C.c_int64, I]),
     "mstress_profile": (I, [P, P, I, I, PD]),
     "mstress_apply_noalloc": (I, [P, I, I, P, P, P]),
     "mstress_sol_phase_ms": (I, [P, PD]),

@@ -102,6 +102,12 @@ class Context:
     def sync(self):
         self._check(self.lib.mstress_sync(self.h))
 
+    def set_wait_limit(self, limit_ns: int = 2_000_000_000, withhold_next: bool = False):
+        """Device-time limit of the solver's grid-barrier waits; withhold_next
+        makes the next persistent launch's wait run out (testing the timeout
+        path)."""
+        self._check(self.lib.mstress_set_wait_limit(self.h, int(limit_ns), int(withhold_next)))
+
     # ------------------------------------------------------- local stage
     def build_block(self, spec: BlockSpec, materials=MATERIALS, mat_id: np.ndarray | None = None,
                     allow_not_converged=False) -> "Block":

@@ -120,6 +120,11 @@ struct TypeTab {             // block models of a solve, by type index
 struct mstress_ctx_s {
     int device = 0;
     int num_sms = 0;
+    // bounded device waits of the persistent solver: a grid-barrier wait gives
+    // up after wait_limit_ns; withhold_next: the next persistent launch's last
+    // CTA skips its first barrier arrival once (test hook for the timeout path)
+    long long wait_limit_ns = 2000000000LL;
+    int withhold_next = 0;
     cudaStream_t stream = nullptr;
     mstress_opts opts{};
     size_t in_use = 0, peak = 0;

@@ -491,7 +491,7 @@ void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool
     if (prec == MSTRESS_FP64) {
         MS_REQUIRE(!vec_fp32, MSTRESS_EINVAL, "FP64 apply needs FP64 vectors");
         ApplyArgs a = apply_args(s, x, z, st, Y, false);
-        if (m <= 80)
+        if (apply_rpt(m, 8, 1) == 2)
             launch_with_smem(k_apply64<2>, s, (size_t)(m * kTile64 + 16 * m) * sizeof(double), a, (m + 15) / 16);
         else
             launch_with_smem(k_apply64<4>, s, (size_t)(m * kTile64 + 32 * m) * sizeof(double), a, (m + 31) / 32);
@@ -504,7 +504,7 @@ void launch_apply(mstress_sol_s* s, int prec, const void* x, const void* z, bool
     }
     ApplyArgs a = apply_args(s, x, z, st, Y, false);
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
-    if (m <= 80) {
+    if (apply_rpt(m, 4, ns) == 2) {
         const size_t smem = (size_t)ns * (m * kTile64 + 16 * m) * sizeof(float);
         const int panels = (m + 15) / 16;
         if (prec == MSTRESS_TF32) launch_with_smem(k_apply32<2, MSTRESS_TF32>, s, smem, a, panels);
@@ -631,7 +631,10 @@ void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
     int* flag = s->flag.as<int>();
     // preferred: one persistent cooperative launch for the whole run
     if (pcg_run_persistent(s, v, prec, max_iter, std::is_same<V, float>::value)) {
+        MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
         MS_CUDA(cudaStreamSynchronize(stream));
+        MS_REQUIRE(s->ctx->h_flag[2] == 0, MSTRESS_EDEVICE_TIMEOUT,
+                   "a tensor-core wait or a grid barrier timed out on the device");
         return;
     }
     if (stream != nullptr && !s->graph[gi] && !s->no_while[gi]) s->no_while[gi] = !build_while_graph<V>(s, v, prec, gi, max_iter);
@@ -1160,6 +1163,17 @@ int mstress_sol_info(mstress_sol sol, int array, int* iters, int* outer, double*
     if (outer) *outer = r.outer;
     if (rel_res) *rel_res = r.rel_res;
     if (status) *status = r.status;
+    return MSTRESS_OK;
+}
+
+int mstress_set_wait_limit(mstress_ctx ctx, int64_t limit_ns, int withhold_next) {
+    if (!ctx) return MSTRESS_EINVAL;
+    if (limit_ns <= 0) {
+        ctx->last_error = "the wait limit must be positive";
+        return MSTRESS_EINVAL;
+    }
+    ctx->wait_limit_ns = limit_ns;
+    ctx->withhold_next = withhold_next ? 1 : 0;
     return MSTRESS_OK;
 }
 

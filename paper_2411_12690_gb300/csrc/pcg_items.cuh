@@ -53,12 +53,31 @@ __device__ __forceinline__ double cta_fold8(const double* v, int n, double* sh8)
 // thread; sh16 as sh8 above.
 __device__ __forceinline__ void cta_fold8_2(const double* v1, const double* v2, int n, double* sh16, double& t1,
                                             double& t2) {
-    const int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < 8) {
-        const int b = (int)((long long)n * w / 8), e = (int)((long long)n * (w + 1) / 8);
-        const double s1 = warp_fold(v1 + b, e - b);
-        const double s2 = warp_fold(v2 + b, e - b);
-        if ((threadIdx.x & 31) == 0) {
+        // warp_fold of both slices with all their loads in flight together
+        const int b = (int)((long long)n * w / 8), e = (int)((long long)n * (w + 1) / 8), cnt = e - b;
+        double s1 = 0, s2 = 0;
+        for (int i0 = lane; i0 < cnt; i0 += 256) {
+            double a1[8], a2[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool in = i0 + 32 * u < cnt;
+                a1[u] = in ? __ldcg(v1 + b + i0 + 32 * u) : 0.0;
+                a2[u] = in ? __ldcg(v2 + b + i0 + 32 * u) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + 32 * u < cnt) {
+                    s1 += a1[u];
+                    s2 += a2[u];
+                }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
             sh16[w] = s1;
             sh16[8 + w] = s2;
         }

@@ -57,6 +57,8 @@ struct PcgArgs {
     int* abort;
     int max_loops;
     int resident;              // two-phase iteration, one array: vector slices may stay in shared memory
+    long long wait_limit_ns;   // a grid-barrier wait gives up after this long
+    int withhold_cta;          // this CTA skips its first barrier arrival (test hook), or -1
     unsigned long long* timers;   // optional: ns spent in phases A, B, C and the loop count (two-phase
                                   // iteration: A, B, and C = 0)
 };
@@ -84,26 +86,33 @@ __device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned
 // k-th barrier of a launch every CTA adds 1 and waits until the counter
 // reaches (k+1) * gridDim.x (compared as a signed difference, so the counter
 // may wrap). The last arrival needs one atomic round trip, the others see it
-// on their next poll. *k_bar is the CTA's barrier count (shared). Returns
-// false (in every thread of the CTA) when the grid is aborting or the wait
-// expired.
+// on their next poll. A wait longer than wait_limit_ns (device clock) gives
+// up: it records the error, raises the abort flag that every other waiting
+// CTA polls, and the kernel returns. *k_bar is the CTA's barrier count
+// (shared). Returns false (in every thread of the CTA) when the grid is
+// aborting or the wait expired.
 __device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok, unsigned* k_bar) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned target = (*k_bar + 1u) * gridDim.x;
+        const bool withhold = *k_bar == 0u && (int)blockIdx.x == a.withhold_cta;
         *k_bar += 1u;
         volatile unsigned* ctr = a.bar;
         __threadfence();
-        if ((int)(atomicAdd(a.bar, 1u) + 1u - target) < 0) {
+        const unsigned arrived = withhold ? *ctr : atomicAdd(a.bar, 1u) + 1u;
+        if ((int)(arrived - target) < 0) {
             long long spins = 0;
+            const unsigned long long t0 = global_ns();
             while ((int)(*ctr - target) < 0) {
-                if ((spins & 63) == 63 && *(volatile int*)a.abort) { ok = 0; break; }
-                if (++spins > (1LL << 25)) {
-                    atomicExch(a.err, 2);
-                    atomicExch(a.abort, 1);
-                    ok = 0;
-                    break;
+                if ((++spins & 63) == 0) {
+                    if (*(volatile int*)a.abort) { ok = 0; break; }
+                    if ((long long)(global_ns() - t0) > a.wait_limit_ns) {
+                        atomicExch(a.err, 2);
+                        atomicExch(a.abort, 1);
+                        ok = 0;
+                        break;
+                    }
                 }
                 __nanosleep(32);
             }
@@ -317,6 +326,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         }
     }
     __syncthreads();
+    // the CTA's first tile, read once (every iteration starts with it)
+    const ApplyWork first_tile = (AM == AM_TC && (int)blockIdx.x < a.apply_items) ? a.ap.work[blockIdx.x] : ApplyWork{};
     unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
     unsigned long long t_acc[4] = {0, 0, 0, 0};
     for (int loop = 0; loop < a.max_loops; ++loop) {
@@ -325,7 +336,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         ArrayCursor curA{solo ? 0 : -1, 0};   // two-phase iteration: groups done per array (alpha fold)
         for (int w = blockIdx.x; w < a.apply_items; w += gridDim.x) {
             if constexpr (AM == AM_TC) {
-                const ApplyWork it = a.ap.work[w];
+                const ApplyWork it = w == (int)blockIdx.x ? first_tile : a.ap.work[w];
                 if (!solo && it.array != curA.k) switch_array(curA, it.array, 3);
                 if (!s_active) continue;
                 if (!ai::apply_tc_item<MODE>(a.ap, a.sh, it, ts, base, offs)) {
@@ -552,8 +563,12 @@ bool launch_coop(KER kernel, mstress_sol_s* s, PcgArgs& a, size_t smem, int need
     if (e != cudaSuccess || per_sm < 1) { cudaGetLastError(); return false; }
     if (tmem_cols > 0) per_sm = std::min(per_sm, 512 / tmem_cols);
     per_sm = std::min(per_sm, 4);   // more CTAs only lengthen the barriers
-    void* args[] = {&a};
     const int grid = std::max(1, std::min(needed, per_sm * s->ctx->num_sms));
+    if (s->ctx->withhold_next) {   // test hook: the last CTA skips its first barrier arrival once
+        a.withhold_cta = grid - 1;
+        s->ctx->withhold_next = 0;
+    }
+    void* args[] = {&a};
     e = cudaLaunchCooperativeKernel((void*)kernel, grid, NT, args, smem, s->ctx->stream);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     note_launches(1);
@@ -592,6 +607,8 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     a.abort = flag + 7;
     a.bar = s->barrier.as<unsigned>();
     a.max_loops = max_iter + 1;
+    a.wait_limit_ns = s->ctx->wait_limit_ns;
+    a.withhold_cta = -1;
     a.timers = s->timers.as<unsigned long long>();
     MS_CUDA(cudaMemsetAsync(flag + 7, 0, sizeof(int), s->ctx->stream));
     MS_CUDA(cudaMemsetAsync(s->barrier.ptr, 0, s->barrier.bytes, s->ctx->stream));
@@ -599,7 +616,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
     const int m = s->m;
     const int vneed = s->n_vwork;
     if (!vec_fp32) {
-        if (m <= 80) {
+        if (apply_rpt(m, 8, 1) == 2) {
             a.panels = (m + 15) / 16;
             a.apply_items = s->n_awork * a.panels;
             const size_t smem = (size_t)(m * kTile64 + 16 * m) * sizeof(double) + 1024;
@@ -653,7 +670,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
         }
     }
     const int ns = prec == MSTRESS_BF16X3 ? 2 : 1;
-    const int rpt = m <= 80 ? 2 : 4;
+    const int rpt = apply_rpt(m, 4, ns);
     a.panels = (m + 8 * rpt - 1) / (8 * rpt);
     a.apply_items = s->n_awork * a.panels;
     const size_t smem = (size_t)ns * (m * kTile64 + 8 * rpt * m) * sizeof(float) + 1024;

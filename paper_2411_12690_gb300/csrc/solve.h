@@ -16,6 +16,16 @@ constexpr int kVecChunk64 = 2048;
 constexpr int kVecChunkTC = 2560;
 constexpr int kVecChunk32 = 4096;
 constexpr int kTile64 = 32;       // blocks per CUDA-core apply / recovery tile
+
+// Rows per panel of the CUDA-core apply (8 x RPT): 32-row panels (RPT = 4)
+// for mid-size bases, 16-row panels (RPT = 2) for small ones and for bases
+// whose 32-row panel would not fit in shared memory next to the coefficient
+// tile (bytes = (m x 32 + rows x m) x element size, at most 200 KB).
+inline int apply_rpt(int m, int elem_bytes, int planes) {
+    if (m <= 80) return 2;
+    const long long need = (long long)planes * (m * 32LL + 32LL * m) * elem_bytes;
+    return need <= 200 * 1024 - 1024 ? 4 : 2;
+}
 constexpr int kTileTC = 128;      // blocks per tensor-core apply tile (the MMA M dimension)
 
 struct ArrayResult {
