@@ -268,10 +268,17 @@ __device__ __forceinline__ void gather_operand(const float* __restrict__ x, cons
 // produce are never read back. GU values per thread are loaded before any is
 // stored (one round of loads per GU * blockDim.x values). With sP, the FP32
 // values are also kept at sP[row * ldp + k].
+// (p, z) pairs: the direction update from one 8-byte load.
+__device__ __forceinline__ float gather_pz(const float2* pz, long long g, float beta) {
+    const float2 v = __ldcg(pz + g);
+    return p_next(v.y, v.x, beta);
+}
+
 template <int MODE, int GU>
 __device__ __forceinline__ void gather_rows(const float* __restrict__ x, const float* __restrict__ z, float beta,
                                             int m, int count, const long long* base, const int* offs, int nkg,
-                                            uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo, float* sP, int ldp) {
+                                            uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo, float* sP, int ldp,
+                                            const float2* pz = nullptr) {
     using OM = OperandMap<MODE>;
     const int total = nkg * count * OM::KE;
     for (int idx0 = threadIdx.x; idx0 < total; idx0 += (int)blockDim.x * GU) {
@@ -283,7 +290,7 @@ __device__ __forceinline__ void gather_rows(const float* __restrict__ x, const f
             if (idx < total) {
                 const int q = idx >> OM::LGKE, kg = q / count, row = q - kg * count;
                 const int k = (kg << OM::LGKE) + (idx & (OM::KE - 1));
-                if (k < m) v[u] = gather(x, z, base[row] + offs[k], beta);
+                if (k < m) v[u] = pz ? gather_pz(pz, base[row] + offs[k], beta) : gather(x, z, base[row] + offs[k], beta);
             }
         }
 #pragma unroll
@@ -352,7 +359,7 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
     __syncthreads();
     const bool dots = a.gpart != nullptr && ts.sP != nullptr;
     gather_rows<MODE, 12>(x, z, beta, m, it.count, base, offs, sh.kpad * sh.esz / 16, ts.sA, sh.a_plane,
-                          tc::sbo_bytes(sh.kpad, sh.esz), dots ? ts.sP : nullptr, ts.ldp);
+                          tc::sbo_bytes(sh.kpad, sh.esz), dots ? ts.sP : nullptr, ts.ldp, a.pz);
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();

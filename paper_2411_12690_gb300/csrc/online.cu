@@ -161,6 +161,7 @@ struct VecArgs {
     const double* dinv;
     const void* dinv_v;     // dinv in the vector precision
     void *x, *r, *z, *p, *q;
+    void* pz;               // optional: (p, z) pairs of the two-phase tensor-core solver (FP32)
     const void* rhs;        // init / residual: right-hand side (FP64)
     double *part_pq, *part_rz, *part_rr;
     int* flag;              // [0] any active, [1] CTA ticket, [2] device error, [3] loop count
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(const __grid_constant__ V
             r[g] = rv;
             z[g] = zv;
             p[g] = (V)0;
+            if (a.pz) static_cast<float2*>(a.pz)[g] = make_float2(0.f, (float)zv);
             srz += (double)rv * (double)zv;
             srr += (double)rv * (double)rv;
         }
@@ -440,6 +442,7 @@ VecArgs vec_args(mstress_sol_s* s, PcgVectors& v) {
     a.z = v.z.ptr;
     a.p = v.p.ptr;
     a.q = v.q.ptr;
+    a.pz = &v == &s->v32 ? s->pz.ptr : nullptr;
     a.part_pq = s->part.as<double>();
     a.part_rz = a.part_pq + s->n_vwork;
     a.part_rr = a.part_rz + s->n_vwork;
@@ -874,6 +877,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         alloc_into(ctx, s->v32.p, nv * sizeof(float), false);
         alloc_into(ctx, s->v32.q, nv * sizeof(float), false);
         alloc_into(ctx, s->v32.state, s->n_arrays * sizeof(PcgState));
+        if (s->use_tc && !tc_streamed(s->m)) alloc_into(ctx, s->pz, nv * sizeof(float2), false);
     }
     if (s->inner64) {
         alloc_into(ctx, s->v64i.x, nv * sizeof(double));

@@ -111,6 +111,32 @@ __device__ __forceinline__ double block_sum(DotAcc<float> v, double* sh) {
     return t;
 }
 
+// Two block sums at once (the <r,z> and <r,r> shares of a work item): each
+// gives exactly block_sum's value, with one pair of barriers for both.
+// sh holds 2 * (blockDim.x / 32) doubles. Results valid in thread 0.
+__device__ __forceinline__ void block_sum2(DotAcc<float> a, DotAcc<float> b, double* sh, double& ta, double& tb) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ahi = __shfl_xor_sync(0xffffffffu, a.hi, o), alo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        const float bhi = __shfl_xor_sync(0xffffffffu, b.hi, o), blo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+        a.merge(ahi, alo);
+        b.merge(bhi, blo);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh[w] = (double)a.hi + (double)a.lo;
+        sh[nw + w] = (double)b.hi + (double)b.lo;
+    }
+    __syncthreads();
+    ta = 0;
+    tb = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nw; ++k) {
+            ta += sh[k];
+            tb += sh[nw + k];
+        }
+}
+
 __device__ __forceinline__ double block_sum(DotAcc<double> v, double* sh);
 
 // Block sum (blockDim.x threads, multiple of 32) in a fixed order; result valid in all threads.
@@ -226,79 +252,13 @@ __device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev
     return acc;
 }
 
-// Interface sum fused with the vector update (the second phase of the
-// two-phase iteration, whose step length alpha = <r,z> / sum_e p_e^T Y_e was
-// folded from the element products): per DOF, p = z + beta p (the same fused
-// multiply-add as the apply's gather), q = sum of the owners' Y_e (masked on
-// constrained rows, never stored), x += alpha p, r -= alpha q, z = D^-1 r; p,
-// x, r, z are stored and this thread's shares of <r,z> and <r,r> returned.
-// Arithmetic in the vector precision V, the same operations as isum_item then
-// vec1_item. U DOFs per thread with all their loads issued first.
-template <int U, class V>
-__device__ __forceinline__ void isum_update_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm,
-                                                 const V* __restrict__ dinv, int ldY, const V* __restrict__ Y,
-                                                 V* __restrict__ p, V* __restrict__ z, V* __restrict__ x,
-                                                 V* __restrict__ r, V beta, V al, DotAcc<V>& srz, DotAcc<V>& srr) {
-    const int n = lm->n, n1 = n - 1;
-    const int16_t* __restrict__ surf = lm->surf_idx;
-    const long long end = it.start + it.count;
-    srz = DotAcc<V>();
-    srr = DotAcc<V>();
-    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
-        V s[U], dv[U], pv[U], zv[U], xv[U], rv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long g = g0 + (long long)u * blockDim.x;
-            s[u] = V(0);
-            dv[u] = V(0);
-            pv[u] = zv[u] = xv[u] = rv[u] = V(0);
-            if (g < end) {
-                dv[u] = dinv[g];
-                pv[u] = p[g];
-                zv[u] = z[g];
-                xv[u] = x[g];
-                rv[u] = r[g];
-                int comp, gx, gy, gz;
-                lattice_coords(A, g, comp, gx, gy, gz);
-                const int ih0 = gx / n1, jh0 = gy / n1;
-                const int ih = min(ih0, A.nx - 1), jh = min(jh0, A.ny - 1);
-                const int il = max((gx % n1 == 0) ? ih0 - 1 : ih0, 0), jl = max((gy % n1 == 0) ? jh0 - 1 : jh0, 0);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int j = (c >> 1) ? jh : jl, i = (c & 1) ? ih : il;
-                    const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
-                    if (use) {
-                        const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
-                        if (sidx >= 0) s[u] += __ldcg(Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long g = g0 + (long long)u * blockDim.x;
-            if (g < end) {
-                const V qv = dv[u] != V(0) ? s[u] : V(0);
-                const V pn = p_next(zv[u], pv[u], beta);
-                const V rn = fma(-al, qv, rv[u]);
-                const V zn = dv[u] * rn;
-                p[g] = pn;
-                x[g] = fma(al, pn, xv[u]);
-                r[g] = rn;
-                z[g] = zn;
-                srz.add(rn, zn);
-                srr.add(rn, rn);
-            }
-        }
-    }
-}
-
 // Resident vector slice: when a CTA keeps one vector work item for a whole
 // solve, the item's x, r and D^-1 stay in shared memory (only this CTA reads
 // or writes them) and the element-product offsets of each DOF's owners are
-// computed once. resident_setup fills them; resident_update_item is then the
-// same arithmetic as isum_update_item (same owner order, same operations), with
-// only p and z (which the apply of every CTA gathers) in global memory.
+// computed once. resident_setup fills them; resident_update_item_pz (below)
+// is then the same arithmetic as isum_update_item_pz (same owner order, same
+// operations), with only the (p, z) pairs, which the apply of every CTA
+// gathers, in global memory.
 // soff[c * stride + l]: offset into Y of owner c of DOF start + l, or -1.
 template <class V>
 __device__ __forceinline__ void resident_setup(const ArrayDev& A, const LocalMap* lm, int ldY, long long start,
@@ -330,23 +290,92 @@ __device__ __forceinline__ void resident_setup(const ArrayDev& A, const LocalMap
     }
 }
 
-template <int U, class V>
-__device__ __forceinline__ void resident_update_item(long long start, int count, const int* __restrict__ soff,
-                                                     int stride, const V* sd, V* sx, V* sr, const V* __restrict__ Y,
-                                                     V* __restrict__ p, V* __restrict__ z, V beta, V al,
-                                                     DotAcc<V>& srz, DotAcc<V>& srr) {
-    srz = DotAcc<V>();
-    srr = DotAcc<V>();
+// Interface sum fused with the vector update (the second phase of the
+// two-phase iteration, whose step length alpha = <r,z> / sum_e p_e^T Y_e was
+// folded from the element products), on (p, z) pairs (float2 per DOF): per
+// DOF, p = z + beta p (the same fused multiply-add as the apply's gather),
+// q = sum of the owners' Y_e in fixed order (masked on constrained rows, never
+// stored), x += alpha p, r -= alpha q, z = D^-1 r; the pair, x and r are
+// stored and this thread's shares of <r,z> and <r,r> returned. U = 5 DOFs
+// per thread with all their loads issued first. The resident variant reads x,
+// r, D^-1 and the owner offsets from shared memory (resident_setup).
+__device__ __forceinline__ void isum_update_item_pz(const VecWork& it, const ArrayDev& A, const LocalMap* lm,
+                                                    const float* __restrict__ dinv, int ldY,
+                                                    const float* __restrict__ Y, float2* __restrict__ pz,
+                                                    float* __restrict__ x, float* __restrict__ r, float beta,
+                                                    float al, DotAcc<float>& srz, DotAcc<float>& srr) {
+    constexpr int U = 5;
+    const int n = lm->n, n1 = n - 1;
+    const int16_t* __restrict__ surf = lm->surf_idx;
+    const long long end = it.start + it.count;
+    srz = DotAcc<float>();
+    srr = DotAcc<float>();
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
+        float s[U], dv[U], xv[U], rv[U];
+        float2 pzv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            s[u] = 0.f;
+            dv[u] = xv[u] = rv[u] = 0.f;
+            pzv[u] = make_float2(0.f, 0.f);
+            if (g < end) {
+                dv[u] = dinv[g];
+                pzv[u] = pz[g];
+                xv[u] = x[g];
+                rv[u] = r[g];
+                int comp, gx, gy, gz;
+                lattice_coords(A, g, comp, gx, gy, gz);
+                const int ih0 = gx / n1, jh0 = gy / n1;
+                const int ih = min(ih0, A.nx - 1), jh = min(jh0, A.ny - 1);
+                const int il = max((gx % n1 == 0) ? ih0 - 1 : ih0, 0), jl = max((gy % n1 == 0) ? jh0 - 1 : jh0, 0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = (c >> 1) ? jh : jl, i = (c & 1) ? ih : il;
+                    const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
+                    if (use) {
+                        const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
+                        if (sidx >= 0) s[u] += __ldcg(Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                const float qv = dv[u] != 0.f ? s[u] : 0.f;
+                const float pn = p_next(pzv[u].y, pzv[u].x, beta);
+                const float rn = fmaf(-al, qv, rv[u]);
+                const float zn = dv[u] * rn;
+                pz[g] = make_float2(pn, zn);
+                x[g] = fmaf(al, pn, xv[u]);
+                r[g] = rn;
+                srz.add(rn, zn);
+                srr.add(rn, rn);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void resident_update_item_pz(long long start, int count, const int* __restrict__ soff,
+                                                        int stride, const float* sd, float* sx, float* sr,
+                                                        const float* __restrict__ Y, float2* __restrict__ pz,
+                                                        float beta, float al, DotAcc<float>& srz,
+                                                        DotAcc<float>& srr) {
+    constexpr int U = 5;
+    srz = DotAcc<float>();
+    srr = DotAcc<float>();
     for (int l0 = threadIdx.x; l0 < count; l0 += (int)blockDim.x * U) {
-        V s[U], pv[U], zv[U];
+        float s[U];
+        float2 pzv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int l = l0 + u * (int)blockDim.x;
-            s[u] = V(0);
-            pv[u] = zv[u] = V(0);
+            s[u] = 0.f;
+            pzv[u] = make_float2(0.f, 0.f);
             if (l < count) {
-                pv[u] = p[start + l];
-                zv[u] = z[start + l];
+                pzv[u] = pz[start + l];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int off = soff[c * stride + l];
@@ -358,14 +387,13 @@ __device__ __forceinline__ void resident_update_item(long long start, int count,
         for (int u = 0; u < U; ++u) {
             const int l = l0 + u * (int)blockDim.x;
             if (l < count) {
-                const V dv = sd[l];
-                const V qv = dv != V(0) ? s[u] : V(0);
-                const V pn = p_next(zv[u], pv[u], beta);
-                const V rn = fma(-al, qv, sr[l]);
-                const V zn = dv * rn;
-                p[start + l] = pn;
-                z[start + l] = zn;
-                sx[l] = fma(al, pn, sx[l]);
+                const float dv = sd[l];
+                const float qv = dv != 0.f ? s[u] : 0.f;
+                const float pn = p_next(pzv[u].y, pzv[u].x, beta);
+                const float rn = fmaf(-al, qv, sr[l]);
+                const float zn = dv * rn;
+                pz[start + l] = make_float2(pn, zn);
+                sx[l] = fmaf(al, pn, sx[l]);
                 sr[l] = rn;
                 srz.add(rn, zn);
                 srr.add(rn, rn);

@@ -11,6 +11,8 @@
 //      G_e^T Y_e (not stored), x += alpha p, r -= alpha q, z = D^-1 r and the
 //      <r,z>, <r,r> partials, folded into beta, the stopping test and the
 //      iteration count.
+// p and z are kept as (p, z) pairs, so that the gather of phase A reads both
+// with one load.
 // Otherwise an iteration has three phases separated by a grid barrier:
 //   A  element products Y_e = A_element p_e (p = z + beta p formed in the
 //      gather), on FP64 CUDA cores, reduced-precision CUDA cores or tcgen05;
@@ -82,29 +84,43 @@ __device__ __forceinline__ void phase_mark(const PcgArgs& a, int phase, unsigned
     }
 }
 
-// Grid barrier with a bounded wait, on one counter that only grows: in the
-// k-th barrier of a launch every CTA adds 1 and waits until the counter
-// reaches (k+1) * gridDim.x (compared as a signed difference, so the counter
-// may wrap). The last arrival needs one atomic round trip, the others see it
-// on their next poll. A wait longer than wait_limit_ns (device clock) gives
-// up: it records the error, raises the abort flag that every other waiting
-// CTA polls, and the kernel returns. *k_bar is the CTA's barrier count
-// (shared). Returns false (in every thread of the CTA) when the grid is
-// aborting or the wait expired.
+// Grid barrier with a bounded wait, on kBarLanes arrival counters that only
+// grow (128 bytes apart, so that the CTAs' atomics spread over several L2
+// lines instead of queueing on one): CTA c adds 1 to counter c % kBarLanes in
+// every barrier, and the k-th barrier of a launch is passed when counter j
+// has reached k * n_j, n_j = the number of CTAs with c % kBarLanes == j
+// (compared as signed differences, so the counters may wrap). Lane j of the
+// CTA's first warp polls counter j. A wait longer than wait_limit_ns (device
+// clock) gives up: it records the error, raises the abort flag that every
+// other waiting CTA polls, and the kernel returns. *k_bar is the CTA's
+// barrier count (shared). Returns false (in every thread of the CTA) when the
+// grid is aborting or the wait expired.
+constexpr int kBarLanes = 8;
+constexpr int kBarStride = 32;   // unsigned words between counters (128 bytes)
+
 __device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok, unsigned* k_bar) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned kb = *k_bar + 1u;   // this barrier's ordinal
+        const bool withhold = kb == 1u && (int)blockIdx.x == a.withhold_cta;
+        const unsigned G = gridDim.x;
+        __syncwarp();
+        if (lane == 0) {
+            *k_bar = kb;
+            __threadfence();
+            if (!withhold) atomicAdd(a.bar + (blockIdx.x % kBarLanes) * kBarStride, 1u);
+        }
+        __syncwarp();
         int ok = 1;
-        const unsigned target = (*k_bar + 1u) * gridDim.x;
-        const bool withhold = *k_bar == 0u && (int)blockIdx.x == a.withhold_cta;
-        *k_bar += 1u;
-        volatile unsigned* ctr = a.bar;
-        __threadfence();
-        const unsigned arrived = withhold ? *ctr : atomicAdd(a.bar, 1u) + 1u;
-        if ((int)(arrived - target) < 0) {
+        if (lane < kBarLanes) {
+            const unsigned nj = lane < (int)G ? (G - 1u - (unsigned)lane) / kBarLanes + 1u : 0u;
+            const unsigned target = kb * nj;
+            volatile unsigned* ctr = a.bar + lane * kBarStride;
             long long spins = 0;
-            const unsigned long long t0 = global_ns();
+            unsigned long long t0 = 0;
             while ((int)(*ctr - target) < 0) {
+                if (spins == 0) t0 = global_ns();
                 if ((++spins & 63) == 0) {
                     if (*(volatile int*)a.abort) { ok = 0; break; }
                     if ((long long)(global_ns() - t0) > a.wait_limit_ns) {
@@ -116,10 +132,14 @@ __device__ __forceinline__ bool grid_sync(const PcgArgs& a, int* s_ok, unsigned*
                 }
                 __nanosleep(32);
             }
+            __threadfence();   // acquire: this lane observed its counter's arrivals
         }
-        __threadfence();
-        if (*(volatile int*)a.abort) ok = 0;
-        *s_ok = ok;
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            __threadfence();
+            if (*(volatile int*)a.abort) ok = 0;
+            *s_ok = ok;
+        }
     }
     __syncthreads();
     return *s_ok != 0;
@@ -136,7 +156,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ long long base[kTileTC], s_eidx[kTileTC];
     __shared__ __align__(16) int offs[3 * kMaxSurf];
-    __shared__ double shr[NT / 32], sh8[16];
+    __shared__ double shr[2 * (NT / 32)], sh8[16];
     __shared__ int s_flag, s_ok, s_active;
     __shared__ unsigned s_kbar;   // grid barriers passed by this CTA
     __shared__ double s_scalar, s_scalar2;
@@ -398,12 +418,12 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             ArrayCursor cur{solo ? 0 : -1, 0};
             if (resident) {
                 if ((int)blockIdx.x < a.n_vwork && s_active) {
-                    pi::DotAcc<V> srz, srr;
-                    pi::resident_update_item<5, V>(v_start, v_count, sOff, kVecChunkTC, sVd, sVx, sVr,
-                                                   static_cast<const V*>(a.ap.Y), p, z, (V)s_scalar2, (V)s_scalar,
-                                                   srz, srr);
-                    const double rz = pi::block_sum(srz, shr);
-                    const double rr = pi::block_sum(srr, shr);
+                    pi::DotAcc<float> srz, srr;
+                    pi::resident_update_item_pz(v_start, v_count, sOff, kVecChunkTC, sVd, sVx, sVr,
+                                                static_cast<const float*>(a.ap.Y), const_cast<float2*>(a.ap.pz),
+                                                (float)s_scalar2, (float)s_scalar, srz, srr);
+                    double rz, rr;
+                    pi::block_sum2(srz, srr, shr, rz, rr);
                     if (tid == 0) {
                         a.part_rz[blockIdx.x] = rz;
                         a.part_rr[blockIdx.x] = rr;
@@ -414,12 +434,13 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
                 const VecWork it = a.vwork[w];
                 if (it.array != cur.k) switch_array(cur, it.array, 2);
                 if (!s_active) continue;
-                pi::DotAcc<V> srz, srr;
-                pi::isum_update_item<5, V>(it, s_A, a.lm, static_cast<const V*>(a.dinv), a.ap.ldY,
-                                           static_cast<const V*>(a.ap.Y), p, z, x, r, (V)s_scalar2, (V)s_scalar, srz,
-                                           srr);
-                const double rz = pi::block_sum(srz, shr);
-                const double rr = pi::block_sum(srr, shr);
+                pi::DotAcc<float> srz, srr;
+                pi::isum_update_item_pz(it, s_A, a.lm, static_cast<const float*>(a.dinv), a.ap.ldY,
+                                        static_cast<const float*>(a.ap.Y), const_cast<float2*>(a.ap.pz),
+                                        reinterpret_cast<float*>(x), reinterpret_cast<float*>(r), (float)s_scalar2,
+                                        (float)s_scalar, srz, srr);
+                double rz, rr;
+                pi::block_sum2(srz, srr, shr, rz, rr);
                 if (tid == 0) {
                     a.part_rz[w] = rz;
                     a.part_rr[w] = rr;
@@ -652,6 +673,8 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
         a.apply_items = s->n_awork_tc;
         a.panels = 1;
         a.ap.gpart = s->gpart.as<double>();     // two-phase iteration: group sums of p_e^T Y_e
+        a.ap.pz = s->pz.as<float2>();           // and the (p, z) pairs
+        if (!a.ap.pz) return false;
         size_t smem = a.sh.smem + a.sh.dot_smem;
         // resident vector slices: one array whose element-product offsets fit in 32 bits
         const size_t vec_smem = (size_t)kVecChunkTC * (3 * sizeof(float) + 4 * sizeof(int));

@@ -55,6 +55,7 @@ struct ApplyArgs {
     void* Y;               // element products [block][ldY]
     int* err;              // device error word (bounded waits)
     double* gpart;         // optional: per 8-block group sums of p_e^T Y_e (tensor-core apply)
+    const float2* pz;      // optional: gather p = z + beta p from (p, z) pairs instead of x and z
 };
 
 // The search-direction update p = z + beta p in the vector precision (one
@@ -157,6 +158,8 @@ struct mstress_sol_s {
     ms::DBuf Y64own;                      // FP64 element buffer of the mixed modes
     void* Y64 = nullptr;                  // FP64 element products (Y64own, or Y in FP64 mode)
     ms::DBuf Y;                           // element-by-element products [block][ldY]
+    ms::DBuf pz;                          // (p, z) pairs of the two-phase tensor-core solver's inner
+                                          // PCG (float2 per lattice DOF), or empty
     ms::DBuf part;                        // 3 * n_vwork partial sums
     ms::DBuf gpart;                       // n_grp partial sums of p_e^T Y_e per 8-block group
     int n_grp = 0;
