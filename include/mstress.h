@@ -123,14 +123,15 @@ typedef struct {
     int max_iter;         /* PCG iteration limit (inner iterations summed)     */
     double inner_rtol;    /* mixed modes: inner PCG relative tolerance (an inner
                              solve also stops below a tenth of the outer
-                             tolerance)                                     */
+                             tolerance); 0 = by precision: 3e-4 BF16X3, 1e-3
+                             TF32, 1e-2 BF16                                */
     int max_outer;        /* mixed modes: refinement step limit                */
     size_t hbm_budget;    /* bytes this context may hold on the device; 0 = all */
     int offline_max_iter; /* local-stage CG iteration limit                    */
     double offline_rtol;  /* local-stage CG relative tolerance                 */
 } mstress_opts;
 
-/* Fill *o with defaults: FP64, rtol 1e-13, max_iter 20000, inner_rtol 1e-4,
+/* Fill *o with defaults: FP64, rtol 1e-13, max_iter 20000, inner_rtol 0 (by precision),
    max_outer 30, hbm_budget 0, offline_max_iter 20000, offline_rtol 1e-13. */
 int mstress_opts_default(mstress_opts* o);
 

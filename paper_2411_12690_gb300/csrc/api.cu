@@ -165,7 +165,7 @@ int mstress_opts_default(mstress_opts* o) {
     o->precision = MSTRESS_FP64;
     o->rtol = 1e-13;
     o->max_iter = 20000;
-    o->inner_rtol = 1e-4;
+    o->inner_rtol = 0.0;   // per precision (see inner_tolerance)
     o->max_outer = 30;
     o->hbm_budget = 0;
     o->offline_max_iter = 20000;
@@ -177,7 +177,7 @@ static int check_opts(const mstress_opts* o, std::string& why) {
     if (o->precision < MSTRESS_FP64 || o->precision > MSTRESS_BF16X3) { why = "unknown precision mode"; return 0; }
     if (!(o->rtol > 0 && o->rtol < 1)) { why = "rtol must be in (0, 1)"; return 0; }
     if (o->max_iter < 1) { why = "max_iter must be >= 1"; return 0; }
-    if (!(o->inner_rtol > 0 && o->inner_rtol < 1)) { why = "inner_rtol must be in (0, 1)"; return 0; }
+    if (!(o->inner_rtol >= 0 && o->inner_rtol < 1)) { why = "inner_rtol must be in [0, 1)"; return 0; }
     if (o->max_outer < 1) { why = "max_outer must be >= 1"; return 0; }
     if (o->offline_max_iter < 1) { why = "offline_max_iter must be >= 1"; return 0; }
     if (!(o->offline_rtol > 0 && o->offline_rtol < 1)) { why = "offline_rtol must be in (0, 1)"; return 0; }

@@ -1010,6 +1010,20 @@ void refine_start(mstress_sol_s* s) {
 // a5: FP64 residual and stopping test; true if any array takes another step.
 bool refine_check(mstress_sol_s* s) { return outer_check(s, s->Y64, s->ctx->opts.max_outer); }
 
+// Relative tolerance of an inner (reduced-precision) solve: the option, or,
+// when it is 0, a per-precision value near the reduction one refinement step
+// can deliver with that operator (measured at 100x100: BF16X3 3e-4, TF32
+// 1e-3, BF16 1e-2 gave the fewest inner iterations and refinement steps).
+double inner_tolerance(const mstress_sol_s* s) {
+    const double o = s->ctx->opts.inner_rtol;
+    if (o > 0) return o;
+    switch (s->precision) {
+        case MSTRESS_TF32: return 1e-3;
+        case MSTRESS_BF16: return 1e-2;
+        default: return 3e-4;
+    }
+}
+
 // One inner solve A d = r for every array still refining, in the inner
 // precision (FP32 vectors with the reduced-precision operator, or FP64 for
 // inner64), then x += d; inner iterations are added to the per-array counts.
@@ -1022,12 +1036,12 @@ void refine_inner(mstress_sol_s* s) {
     const PcgState* gate = s->v64.state.as<PcgState>();
     PcgVectors& vi = s->inner64 ? s->v64i : s->v32;
     if (s->inner64) {
-        pcg_start<double>(s, vi, s->v64.r.as<double>(), o.inner_rtol, budget, gate);
+        pcg_start<double>(s, vi, s->v64.r.as<double>(), inner_tolerance(s), budget, gate);
         pcg_run<double>(s, vi, MSTRESS_FP64, budget);
         k_correct<double><<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
             s->d_vwork.as<VecWork>(), s->n_vwork, gate, s->v64.x.as<double>(), vi.x.as<double>());
     } else {
-        pcg_start<float>(s, vi, s->v64.r.as<double>(), o.inner_rtol, budget, gate);
+        pcg_start<float>(s, vi, s->v64.r.as<double>(), inner_tolerance(s), budget, gate);
         pcg_run<float>(s, vi, s->precision, budget);
         k_correct<float><<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(
             s->d_vwork.as<VecWork>(), s->n_vwork, gate, s->v64.x.as<double>(), vi.x.as<float>());
@@ -1041,13 +1055,32 @@ void refine_inner(mstress_sol_s* s) {
 }
 
 // True FP64 residual of the final iterate, per-array results, and the
-// prescribed values added back to the solution.
-void solve_finish(mstress_sol_s* s, bool refined) {
+// prescribed values added back to the solution. checked: the refinement loop
+// ended with a check of the current iterate, whose FP64 residual ||b - A x||^2
+// the outer state already holds (so it is not computed again).
+void solve_finish(mstress_sol_s* s, bool refined, bool checked) {
     cudaStream_t stream = s->ctx->stream;
     check_device_error(s);
     std::vector<PcgState> before(s->n_arrays);
     MS_CUDA(cudaMemcpyAsync(before.data(), s->v64.state.ptr, before.size() * sizeof(PcgState), cudaMemcpyDeviceToHost,
                             stream));
+    if (refined && checked) {
+        MS_CUDA(cudaStreamSynchronize(stream));
+        for (int a = 0; a < s->n_arrays; ++a) {
+            ArrayResult& R = s->results[a];
+            R.rel_res = before[a].bb > 0 ? std::sqrt(before[a].rr / before[a].bb) : 0.0;
+            R.outer = before[a].iters;
+            R.status = before[a].status;
+            if (!std::isfinite(R.rel_res)) R.status = MSTRESS_ENUMERIC;
+        }
+        if (s->xbc.ptr) {
+            k_add_bc<<<(unsigned)((s->n_vec + 255) / 256), 256, 0, stream>>>(s->n_vec, s->v64.x.as<double>(),
+                                                                              s->xbc.as<double>());
+            MS_LAUNCH_CHECK();
+            MS_CUDA(cudaStreamSynchronize(stream));
+        }
+        return;
+    }
     launch_apply(s, MSTRESS_FP64, s->v64.x.ptr, nullptr, false, nullptr, s->Y64);
     launch_isum(s, s->Y64, false, s->v64.x.ptr, nullptr, s->v64.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
     VecArgs va = vec_args(s, s->v64);
@@ -1085,15 +1118,19 @@ void run_solve(mstress_sol_s* s) {
     if (s->precision == MSTRESS_FP64) {
         pcg_start<double>(s, s->v64, s->b.as<double>(), o.rtol, o.max_iter, nullptr);
         pcg_run<double>(s, s->v64, MSTRESS_FP64, o.max_iter);
-        solve_finish(s, false);
+        solve_finish(s, false, false);
         return;
     }
     refine_start(s);
+    bool checked = false;
     for (int k = 0; k <= o.max_outer; ++k) {
-        if (!refine_check(s)) break;
+        if (!refine_check(s)) {
+            checked = true;
+            break;
+        }
         refine_inner(s);
     }
-    solve_finish(s, true);
+    solve_finish(s, true, checked);
 }
 
 int solve_common(mstress_ctx ctx, const std::vector<LayoutIn>& in, mstress_sol* out) {

@@ -194,7 +194,7 @@ void solve_prepare(mstress_sol_s* s);
 void refine_start(mstress_sol_s* s);
 bool refine_check(mstress_sol_s* s);
 void refine_inner(mstress_sol_s* s);
-void solve_finish(mstress_sol_s* s, bool refined);
+void solve_finish(mstress_sol_s* s, bool refined, bool checked);
 void check_device_error(mstress_sol_s* s);
 
 // global-stage launches (online.cu)
