@@ -124,7 +124,7 @@ typedef struct {
     double inner_rtol;    /* mixed modes: inner PCG relative tolerance (an inner
                              solve also stops below a tenth of the outer
                              tolerance); 0 = by precision: 3e-4 BF16X3, 1e-3
-                             TF32, 1e-2 BF16                                */
+                             TF32, 3e-2 BF16                                */
     int max_outer;        /* mixed modes: refinement step limit                */
     size_t hbm_budget;    /* bytes this context may hold on the device; 0 = all */
     int offline_max_iter; /* local-stage CG iteration limit                    */

@@ -1012,14 +1012,14 @@ bool refine_check(mstress_sol_s* s) { return outer_check(s, s->Y64, s->ctx->opts
 
 // Relative tolerance of an inner (reduced-precision) solve: the option, or,
 // when it is 0, a per-precision value near the reduction one refinement step
-// can deliver with that operator (measured at 100x100: BF16X3 3e-4, TF32
-// 1e-3, BF16 1e-2 gave the fewest inner iterations and refinement steps).
+// can deliver with that operator (measured on the 100x100 array: BF16X3 3e-4,
+// TF32 1e-3 and BF16 3e-2 gave the shortest solves).
 double inner_tolerance(const mstress_sol_s* s) {
     const double o = s->ctx->opts.inner_rtol;
     if (o > 0) return o;
     switch (s->precision) {
         case MSTRESS_TF32: return 1e-3;
-        case MSTRESS_BF16: return 1e-2;
+        case MSTRESS_BF16: return 3e-2;
         default: return 3e-4;
     }
 }
