@@ -315,7 +315,10 @@ int mstress_launch_count(int64_t* n);
 /* Time one kernel of a finished solve: reps launches between two CUDA events
    on the context stream, *avg_ms = mean duration of one launch. The kernel
    runs on the solution's own scratch vectors (the solution x is not touched).
-     phase 0  operator apply (element products) in the solve's precision
+     phase 0  operator apply (element products) in the solve's precision,
+              gathering p and z as an iteration does (the kernel of the
+              per-phase iteration of large batches; inside the persistent
+              solver the same work is its phase A)
      phase 1  interface sum with the <p, q> partials
      phase 2  operator apply in FP64
      phase 3  von Mises recovery (contraction + epilogue) into scratch */
@@ -324,7 +327,9 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
 /* Time spent inside the persistent solver's iterations of this solution,
    measured on the device at its grid barriers: ms4[0..2] = milliseconds in
    the element products, the interface sum and the vector update (summed over
-   all iterations and refinement steps), ms4[3] = number of iterations. */
+   all iterations and refinement steps), ms4[3] = number of iterations. All
+   zero when the solve ran the per-phase iteration (batches of at least 4096
+   blocks on the streamed tensor-core apply). */
 int mstress_sol_phase_ms(mstress_sol sol, double* ms4);
 
 /* Apply the assembled reduced operator of a layout (one matrix-free K_r apply

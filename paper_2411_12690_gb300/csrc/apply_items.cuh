@@ -691,6 +691,7 @@ __device__ bool tcs_apply_phase(const ApplyArgs& a, const TcsShape& sh, TcsState
             const ApplyWork it = a.work[w];
             if (a.st && !__ldcg(&a.st[it.array].active)) continue;
             bool ok = !*(volatile int*)fail && tc::mbar_wait(ts.accF, tt & 1u, kTries);
+            ok = __all_sync(0xffffffffu, ok);   // tensor-memory loads are warp-collective: stop together
             tc::fence_after();
             if (!ok) {
                 *(volatile int*)fail = 1;

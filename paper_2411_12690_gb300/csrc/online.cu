@@ -609,7 +609,12 @@ bool build_while_graph(mstress_sol_s* s, PcgVectors& v, int prec, int gi, int ma
         if (ok) {
             g_capturing = true;
             try {
-                pcg_iteration<V>(s, v, prec, 1, h, max_iter + 2);
+                if constexpr (std::is_same<V, float>::value) {
+                    if (pcg_wide(s, prec)) pcg_iteration_wide(s, v, prec, 1, h, max_iter + 2);
+                    else pcg_iteration<V>(s, v, prec, 1, h, max_iter + 2);
+                } else {
+                    pcg_iteration<V>(s, v, prec, 1, h, max_iter + 2);
+                }
             } catch (...) {
                 ok = false;
             }
@@ -622,7 +627,7 @@ bool build_while_graph(mstress_sol_s* s, PcgVectors& v, int prec, int gi, int ma
     cudaGraphDestroy(g);
     cudaGetLastError();
     if (!ok) s->graph[gi] = nullptr;
-    s->graph_iters[gi] = 3;   // kernel nodes per loop iteration
+    s->graph_iters[gi] = std::is_same<V, float>::value && pcg_wide(s, prec) ? 5 : 3;   // kernel nodes per loop iteration
     return ok;
 }
 
@@ -632,8 +637,10 @@ void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
     constexpr int gi = std::is_same<V, float>::value ? 1 : 0;
     cudaStream_t stream = s->ctx->stream;
     int* flag = s->flag.as<int>();
-    // preferred: one persistent cooperative launch for the whole run
-    if (pcg_run_persistent(s, v, prec, max_iter, std::is_same<V, float>::value)) {
+    // preferred: one persistent cooperative launch for the whole run, except
+    // for large batches on the streamed apply (per-phase launches, same bits)
+    const bool wide = std::is_same<V, float>::value && pcg_wide(s, prec);
+    if (!wide && pcg_run_persistent(s, v, prec, max_iter, std::is_same<V, float>::value)) {
         MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
         MS_CUDA(cudaStreamSynchronize(stream));
         MS_REQUIRE(s->ctx->h_flag[2] == 0, MSTRESS_EDEVICE_TIMEOUT,
@@ -651,7 +658,15 @@ void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
     // no graph (legacy default stream, or conditional nodes unavailable):
     // launch chunks of iterations and poll the any-active flag between them
     for (int done_iters = 0; done_iters < max_iter + 2; done_iters += kChunkIters) {
-        for (int k = 0; k < kChunkIters; ++k) pcg_iteration<V>(s, v, prec, 0, 0, max_iter + 2);
+        for (int k = 0; k < kChunkIters; ++k) {
+            if constexpr (std::is_same<V, float>::value) {
+                if (wide) {
+                    pcg_iteration_wide(s, v, prec, 0, 0, max_iter + 2);
+                    continue;
+                }
+            }
+            pcg_iteration<V>(s, v, prec, 0, 0, max_iter + 2);
+        }
         MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
         MS_CUDA(cudaStreamSynchronize(stream));
         if (s->ctx->h_flag[0] == 0) break;
@@ -1280,9 +1295,9 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
     if (phase == 3) alloc_into(ctx, out, recover_bytes(s, MSTRESS_VM_ELEM), false);
     auto run = [&]() {
         switch (phase) {
-            case 0:
-                if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, nullptr, true, nullptr, s->Y.ptr);
-                else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, nullptr, false, nullptr, s->Y.ptr);
+            case 0:   // gathering p and z as an iteration does (p = z + beta p, beta = 0 here)
+                if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);
+                else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, s->v64.z.ptr, false, nullptr, s->Y.ptr);
                 break;
             case 1:
                 if (mixed) launch_isum(s, s->Y.ptr, true, s->v32.p.ptr, nullptr, s->v32.q.ptr, true, s->dinv32.ptr,

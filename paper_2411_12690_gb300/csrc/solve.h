@@ -207,6 +207,16 @@ void launch_isum(mstress_sol_s* s, const void* Y, bool y_fp32, void* p, const vo
 // persistent cooperative PCG (pcg_persistent.cu); false if it cannot be launched
 bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter, bool vec_fp32);
 
+// per-phase PCG iteration for large batches on the streamed tensor-core apply
+// (pcg_wide.cu), bitwise equal to the persistent solver's iteration; taken
+// from kWideBlocks blocks on (measured: below, the persistent solver's short
+// iterations win; from about 3 000 blocks of the degree-4 basis on, the
+// occupancy of separate kernels does)
+constexpr int64_t kWideBlocks = 4096;
+bool pcg_wide(const mstress_sol_s* s, int prec);
+void pcg_iteration_wide(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond, cudaGraphConditionalHandle cond,
+                        int loop_cap);
+
 // tensor-core kernels (tc.cu)
 bool tc_supported(int m);
 bool tc_streamed(int m);   // operator streamed along K (large bases) instead of resident

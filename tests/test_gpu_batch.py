@@ -92,3 +92,45 @@ def test_batch_two_block_variants_m294(api):
         bound = vm_bound_rows(ob, types, osol.coeffs[pick], j["dT"], L.MSTRESS_BF16X3)
         err = np.abs(bv[k].reshape(-1, n_el)[pick].astype(np.float64) - ovm)
         assert np.all(err <= bound + 1e-12 * ovm.max())
+
+
+@pytest.mark.parametrize("prec", [L.MSTRESS_BF16X3, L.MSTRESS_TF32])
+def test_large_streamed_batch_per_phase_equals_alone(api, prec):
+    """A batch of 4 113 blocks of the degree-4 basis (m = 294) runs the
+    per-phase iteration (launches of its own per phase: at least 4 096 blocks
+    on the streamed apply), while each of its arrays alone (3 969, 144 and 35
+    blocks) runs the persistent solver: the two paths give bitwise the same
+    element DOFs, von Mises values and iteration counts, and the small arrays
+    match the oracle (element DOFs at 1e-9, sampled von Mises within the
+    per-element rounding bound)."""
+    spec = W.BlockSpec(10.0, 10.0, 30.0, 8, 8, 6, 2.5, 0.5, 4)
+    ctx = api.Context(precision=prec)
+    blks = [ctx.build_block(spec), ctx.build_block(spec.dummy())]
+    jobs = [dict(site_type=W.site_types(63, 63, 0.8, seed=31), blocks=blks, dT=-260.0),
+            dict(site_type=W.site_types(12, 12, 0.7, seed=32), blocks=blks, dT=-180.0),
+            dict(site_type=W.site_types(5, 7, 0.6, seed=33), blocks=blks, dT=-220.0, clamp_top=True)]
+    sizes = [j["site_type"].size for j in jobs]
+    assert sum(sizes) >= 4096 and max(sizes) < 4096
+    batch = ctx.solve_batch(jobs)
+    n_el = spec.ex * spec.ey * spec.ez
+    bc = _per_array(batch, sizes, L.MSTRESS_COEFF, 294)
+    bv = _per_array(batch, sizes, L.MSTRESS_VM_ELEM, n_el)
+    rng = np.random.default_rng(6)
+    for k, j in enumerate(jobs):
+        alone = ctx.solve(j["site_type"], blks, j["dT"], clamp_top=j.get("clamp_top", False))
+        assert alone.info()["status"] == 0 and batch.info(k)["status"] == 0
+        assert batch.info(k)["rel_res"] <= 1e-12
+        assert batch.info(k)["iters"] == alone.info()["iters"]
+        assert np.array_equal(alone.recover(L.MSTRESS_COEFF), bc[k])
+        assert np.array_equal(alone.recover(L.MSTRESS_VM_ELEM), bv[k])
+        if k == 0:
+            continue   # the 63 x 63 array: the oracle's sparse direct solve is too large for a test
+        ob, osol = oracle_solve(spec, j["site_type"], j["dT"], clamp_top=j.get("clamp_top", False))
+        c = bc[k].reshape(-1, 294)
+        assert rel_l2(c, osol.coeffs) <= 1e-9
+        pick = rng.choice(sizes[k], min(6, sizes[k]), replace=False)
+        types = osol.site_type.ravel()[pick]
+        ovm = oracle_vm_rows(ob, types, osol.coeffs[pick], j["dT"])
+        bound = vm_bound_rows(ob, types, osol.coeffs[pick], j["dT"], prec)
+        err = np.abs(bv[k].reshape(-1, n_el)[pick].astype(np.float64) - ovm)
+        assert np.all(err <= bound + 1e-12 * ovm.max())
