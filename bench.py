@@ -644,6 +644,7 @@ def batch_run(prec_name, n_arrays, steps, warmup, local):
             split.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
         infos = [sol.info(a) for a in range(len(jobs))]
         phases = sol.phase_ms()
+        tiling = sol.tiling()
         if k == warmup + steps - 1 and not phases["iterations"]:
             # per-phase iteration: its apply kernel timed alone (CUDA events, context stream)
             phases["apply_kernel_ms"] = api.profile(ctx, sol, 0, 5)
@@ -664,6 +665,7 @@ def batch_run(prec_name, n_arrays, steps, warmup, local):
                                     "per-phase launches in a CUDA graph (k_apply_tcs, k_w_isum, k_w_alpha, "
                                     "k_w_vec, k_w_beta)"),
                       "persistent_phase_ms": phases,
+                      "tc_tile": tiling.get("tc_tile"), "tile_autotuned": tiling.get("tuned"),
                       "l2": "inputs larger than L2 (the batch's vectors and element products exceed 129 MB)"},
            "roofline": batch_roofline(prec, jobs, n_blocks, n_el, phases, rec_ms, clk.get("sm_mhz") or 1900.0),
            "clocks": clk}

@@ -30,6 +30,14 @@ __device__ __forceinline__ V gather(const V* x, const V* z, long long g, V beta)
     return z ? p_next(__ldcg(z + g), __ldcg(x + g), beta) : __ldcg(x + g);
 }
 
+// The same through the read-only L1 path (ld.global.nc), for kernels during
+// which nothing writes x or z (the stand-alone applies): neighbouring
+// coefficients of one sector, read by separate loads, then hit L1.
+template <class V>
+__device__ __forceinline__ V gather_nc(const V* x, const V* z, long long g, V beta) {
+    return z ? p_next(__ldg(z + g), __ldg(x + g), beta) : __ldg(x + g);
+}
+
 // Gather the element DOFs of a tile of (1 << tile_shift) blocks, index
 // idx = k * tile + b, eight values per thread in flight at a time (the loads of
 // a round are independent, so they overlap instead of queueing one L2 round
@@ -539,7 +547,7 @@ struct QuadMap {
     }
 };
 
-template <int MODE, int QU>
+template <int MODE, int QU, bool NC>
 __device__ __forceinline__ void quad_load(const float* __restrict__ x, const float* __restrict__ z, float beta, int m,
                                           int count, const long long* base, const int* offs, int k0, int u0, int nthr,
                                           float (&v)[QU][4]) {
@@ -560,10 +568,17 @@ __device__ __forceinline__ void quad_load(const float* __restrict__ x, const flo
                 o.z = k + 2 < m ? offs[k + 2] : 0;
             }
         }
-        v[q][0] = live && k < m ? gather(x, z, bb + o.x, beta) : 0.f;
-        v[q][1] = live && k + 1 < m ? gather(x, z, bb + o.y, beta) : 0.f;
-        v[q][2] = live && k + 2 < m ? gather(x, z, bb + o.z, beta) : 0.f;
-        v[q][3] = live && k + 3 < m ? gather(x, z, bb + o.w, beta) : 0.f;
+        if constexpr (NC) {
+            v[q][0] = live && k < m ? gather_nc(x, z, bb + o.x, beta) : 0.f;
+            v[q][1] = live && k + 1 < m ? gather_nc(x, z, bb + o.y, beta) : 0.f;
+            v[q][2] = live && k + 2 < m ? gather_nc(x, z, bb + o.z, beta) : 0.f;
+            v[q][3] = live && k + 3 < m ? gather_nc(x, z, bb + o.w, beta) : 0.f;
+        } else {
+            v[q][0] = live && k < m ? gather(x, z, bb + o.x, beta) : 0.f;
+            v[q][1] = live && k + 1 < m ? gather(x, z, bb + o.y, beta) : 0.f;
+            v[q][2] = live && k + 2 < m ? gather(x, z, bb + o.z, beta) : 0.f;
+            v[q][3] = live && k + 3 < m ? gather(x, z, bb + o.w, beta) : 0.f;
+        }
     }
 }
 
@@ -602,8 +617,9 @@ __device__ __forceinline__ void quad_store(int u0, int nthr, const float (&v)[QU
 // thread of the CTA calls this; each takes its role. Returns false if a wait
 // expired (ts.fail set). PREFETCH: the gather loads the next K slot's values
 // while it stores the current one (two register sets); without it (a kernel
-// with less register room) one set.
-template <int MODE, bool PREFETCH = true>
+// with less register room) one set. NC: nothing writes x or z during the
+// kernel, so the gather may read them through L1 (gather_nc).
+template <int MODE, bool PREFETCH = true, bool NC = false>
 __device__ bool tcs_apply_phase(const ApplyArgs& a, const TcsShape& sh, TcsState& ts, long long* base, int* offs,
                                 int w0, int wstride) {
     constexpr bool TF32 = MODE == MSTRESS_TF32;
@@ -729,16 +745,16 @@ __device__ bool tcs_apply_phase(const ApplyArgs& a, const TcsShape& sh, TcsState
             tile_setup_part(a, it, A, base, offs, gt, kTcsGather);
             named_sync(1, kTcsGather);
             float vc[kTcsQU][4], vn[kTcsQU][4];
-            if (PREFETCH) quad_load<MODE, kTcsQU>(x, z, beta, a.m, it.count, base, offs, 0, gt, kTcsGather, vc);
+            if (PREFETCH) quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, 0, gt, kTcsGather, vc);
             bool ok = true;
             for (int c = 0; c < sh.nck; ++c, ++g) {
                 const uint32_t slot = g % S, use = g / S;
                 if (!PREFETCH)   // loads issued before the wait for the slot, so they overlap it
-                    quad_load<MODE, kTcsQU>(x, z, beta, a.m, it.count, base, offs, c * sh.ck, gt, kTcsGather, vc);
+                    quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, c * sh.ck, gt, kTcsGather, vc);
                 if (use > 0) ok = tc::mbar_wait(&ts.empty[slot], (use - 1) & 1u, kTries);
                 if (!ok) break;
                 if (PREFETCH && c + 1 < sh.nck)   // next slot's values in flight while this one is stored
-                    quad_load<MODE, kTcsQU>(x, z, beta, a.m, it.count, base, offs, (c + 1) * sh.ck, gt, kTcsGather,
+                    quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, (c + 1) * sh.ck, gt, kTcsGather,
                                             vn);
                 quad_store<MODE, kTcsQU>(gt, kTcsGather, vc, ts.slots + slot * slot_bytes, sh.a_plane, sbo);
                 tc::fence_smem_async();

@@ -927,10 +927,12 @@ void set_tc_tiles(mstress_sol_s* s, int tile) {
 // Autotuner of the tensor-core tile (the MMA M extent actually filled, i.e.
 // blocks per tile): for each candidate it runs a few iterations of the
 // persistent solver on the solve's own right-hand side and reads the time of
-// the element-product phase from the solver's device timers; the fastest is
-// kept, and cached in the context per (basis size, precision, batch-size
-// class) so later solves of that class skip the search. The trial iterations
-// leave nothing behind: every solve restarts its vectors and scalars.
+// the element-product phase from the solver's device timers (or, when the
+// solve will take the per-phase iteration, times the stand-alone apply kernel
+// with CUDA events); the fastest is kept, and cached in the context per
+// (basis size, precision, batch-size class) so later solves of that class
+// skip the search. The trials leave nothing behind: every solve restarts its
+// vectors and scalars.
 void autotune_tc_tile(mstress_sol_s* s) {
     if (!s->use_tc || s->precision == MSTRESS_FP64 || s->h_seg.empty()) return;
     mstress_ctx ctx = s->ctx;
@@ -952,6 +954,34 @@ void autotune_tc_tile(mstress_sol_s* s) {
     cudaStream_t st = ctx->stream;
     int best = h;
     double best_ns = -1;
+    if (pcg_wide(s, s->precision)) {   // the per-phase iteration's own apply kernel, timed alone
+        pcg_start<float>(s, s->v32, s->b.as<double>(), 0.0, kTrialIters, nullptr);   // p = 0, z = D^-1 b
+        cudaEvent_t e0, e1;
+        MS_CUDA(cudaEventCreate(&e0));
+        MS_CUDA(cudaEventCreate(&e1));
+        for (int c : cand) {
+            if (c < 8 || c > kTileTC) continue;
+            set_tc_tiles(s, c);
+            launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);   // warm-up
+            MS_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; ++r)
+                launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);
+            MS_CUDA(cudaEventRecord(e1, st));
+            MS_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            MS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (best_ns < 0 || ms < best_ns) {
+                best_ns = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        check_device_error(s);
+        ctx->tile_choice[key] = best;
+        if (best != s->tc_tile) set_tc_tiles(s, best);
+        return;
+    }
     for (int c : cand) {
         if (c < 8 || c > kTileTC) continue;
         set_tc_tiles(s, c);

@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(kTcsThreads, 1) k_apply_tcs(const __grid_const
     __syncthreads();
     tc::fence_after();
     ts.tmem = tmem_base;
-    if (!ai::tcs_apply_phase<MODE>(a, sh, ts, base, offs, blockIdx.x, gridDim.x)) {
+    // stand-alone: x and z are not written during the kernel (read through L1)
+    if (!ai::tcs_apply_phase<MODE, true, true>(a, sh, ts, base, offs, blockIdx.x, gridDim.x)) {
         if (tid == 0) atomicExch(a.err, 1);
         ai::tcs_drain(ts, sh);
     }
