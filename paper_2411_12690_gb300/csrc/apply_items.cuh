@@ -315,6 +315,49 @@ __device__ __forceinline__ void gather_rows(const float* __restrict__ x, const f
     }
 }
 
+// gather_rows from (p, z) pairs in two halves, for a tile whose gather is a
+// single round (kpad * count <= GU * blockDim.x): the loads, which need no
+// beta, and then the direction update p = z + beta p with the same FMA and the
+// same stores as gather_rows (so the operands are bitwise the same). Between
+// the halves the caller may wait for beta while the loads are in flight.
+template <int MODE, int GU>
+__device__ __forceinline__ void gather_rows_pz_load(const float2* pz, int m, int count, const long long* base,
+                                                    const int* offs, int nkg, float2 (&w)[GU]) {
+    using OM = OperandMap<MODE>;
+    const int total = nkg * count * OM::KE;
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+        const int idx = (int)threadIdx.x + u * (int)blockDim.x;
+        w[u] = make_float2(0.f, 0.f);
+        if (idx < total) {
+            const int q = idx >> OM::LGKE, kg = q / count, row = q - kg * count;
+            const int k = (kg << OM::LGKE) + (idx & (OM::KE - 1));
+            if (k < m) w[u] = __ldcg(pz + base[row] + offs[k]);
+        }
+    }
+}
+
+template <int MODE, int GU>
+__device__ __forceinline__ void gather_rows_pz_store(const float2 (&w)[GU], float beta, int m, int count, int nkg,
+                                                     uint8_t* plane0, uint32_t plane_bytes, uint32_t sbo, float* sP,
+                                                     int ldp) {
+    using OM = OperandMap<MODE>;
+    const int total = nkg * count * OM::KE;
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+        const int idx = (int)threadIdx.x + u * (int)blockDim.x;
+        if (idx < total) {
+            const int e = idx & (OM::KE - 1), q = idx >> OM::LGKE, kg = q / count, row = q - kg * count;
+            const int k = (kg << OM::LGKE) + e;
+            const float v = k < m ? p_next(w[u].y, w[u].x, beta) : 0.f;
+            const uint32_t off = (uint32_t)(row >> 3) * sbo + (uint32_t)kg * 128u + (uint32_t)(row & 7) * 16u +
+                                 (uint32_t)e * OM::ESZ;
+            put_operand(plane0, plane_bytes, off, v, MODE);
+            if (sP) sP[row * ldp + (kg << OM::LGKE) + e] = v;
+        }
+    }
+}
+
 // Per-CTA tensor-core state that persists across work items.
 struct TcState {
     uint8_t* sA;        // gathered coefficients (NS planes)
@@ -333,25 +376,14 @@ struct TcState {
     const double* beta_pre;  // shared memory by the caller) instead of loading them per tile
 };
 
-// D (128 x npad) = C (tile blocks x K) * K_r^T on the tensor cores for one
-// tile; writes the element products Y of the tile's blocks. Returns false if
-// the MMA completion wait timed out (the caller stops and reports it).
+// Tile set-up of the tensor-core apply: the operator image of the tile's type
+// (when it changes) and the gather offsets (unless this tile's are cached);
+// ends with a CTA barrier.
 template <int MODE>
-__device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape& sh, const ApplyWork& it,
-                                              TcState& ts, long long* base, int* offs) {
-    constexpr bool TF32 = MODE == MSTRESS_TF32;
+__device__ __forceinline__ void apply_tc_setup(const ApplyArgs& a, const TcShape& sh, const ApplyWork& it, TcState& ts,
+                                               long long* base, int* offs) {
     constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    const int m = a.m;
-    const float* __restrict__ x = static_cast<const float*>(a.x);
-    const float* __restrict__ z = static_cast<const float*>(a.z);
-    float* __restrict__ Y = static_cast<float*>(a.Y);
-    float beta;
-    if (ts.A_pre) {
-        beta = ts.beta_pre ? (float)*ts.beta_pre : 0.f;
-    } else {
-        beta = a.st ? (float)a.st[it.array].beta : 0.f;
-    }
+    const int tid = threadIdx.x;
     if (it.type != ts.cur_type) {
         const uint4* src = static_cast<const uint4*>(a.tt.Klp[it.type]);
         for (uint32_t i = tid; i < NS * sh.b_plane / 16; i += blockDim.x) reinterpret_cast<uint4*>(ts.sB)[i] = src[i];
@@ -365,9 +397,43 @@ __device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape&
         ts.cached_array = it.array;
     }
     __syncthreads();
+}
+
+template <int MODE>
+__device__ __forceinline__ bool apply_tc_finish(const ApplyArgs& a, const TcShape& sh, const ApplyWork& it,
+                                                TcState& ts);
+
+// D (128 x npad) = C (tile blocks x K) * K_r^T on the tensor cores for one
+// tile; writes the element products Y of the tile's blocks. Returns false if
+// the MMA completion wait timed out (the caller stops and reports it).
+template <int MODE>
+__device__ __forceinline__ bool apply_tc_item(const ApplyArgs& a, const TcShape& sh, const ApplyWork& it,
+                                              TcState& ts, long long* base, int* offs) {
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    const float* __restrict__ z = static_cast<const float*>(a.z);
+    float beta;
+    if (ts.A_pre) {
+        beta = ts.beta_pre ? (float)*ts.beta_pre : 0.f;
+    } else {
+        beta = a.st ? (float)a.st[it.array].beta : 0.f;
+    }
+    apply_tc_setup<MODE>(a, sh, it, ts, base, offs);
     const bool dots = a.gpart != nullptr && ts.sP != nullptr;
-    gather_rows<MODE, 12>(x, z, beta, m, it.count, base, offs, sh.kpad * sh.esz / 16, ts.sA, sh.a_plane,
+    gather_rows<MODE, 12>(x, z, beta, a.m, it.count, base, offs, sh.kpad * sh.esz / 16, ts.sA, sh.a_plane,
                           tc::sbo_bytes(sh.kpad, sh.esz), dots ? ts.sP : nullptr, ts.ldp, a.pz);
+    return apply_tc_finish<MODE>(a, sh, it, ts);
+}
+
+// The rest of the tile once its operands are in shared memory: the MMAs, the
+// element products Y and (two-phase iteration) the group sums of p_e^T Y_e.
+template <int MODE>
+__device__ __forceinline__ bool apply_tc_finish(const ApplyArgs& a, const TcShape& sh, const ApplyWork& it,
+                                                TcState& ts) {
+    constexpr bool TF32 = MODE == MSTRESS_TF32;
+    constexpr int NS = MODE == MSTRESS_BF16X3 ? 2 : 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    float* __restrict__ Y = static_cast<float*>(a.Y);
+    const bool dots = a.gpart != nullptr && ts.sP != nullptr;
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();

@@ -348,13 +348,40 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     __syncthreads();
     // the CTA's first tile, read once (every iteration starts with it)
     const ApplyWork first_tile = (AM == AM_TC && (int)blockIdx.x < a.apply_items) ? a.ap.work[blockIdx.x] : ApplyWork{};
+    // The beta fold overlapped with the next gather's loads (one array,
+    // resident slices, the CTA's only tile gathered in one round): the (p, z)
+    // loads, which do not need beta, are issued right after the barrier that
+    // precedes the fold, and the direction update p = z + beta p follows it --
+    // the same operations in the same order as without the overlap. (The same
+    // for the alpha fold and the vector phase's loads was measured slower: the
+    // registers the loads hold across the fold push the kernel into spills.)
+    constexpr int kGU = 12;
+    bool ov_a = false;
+    float2 gw[kGU];
+    if constexpr (AM == AM_TC) {
+        ov_a = resident && a.ap.pz && (int)blockIdx.x < a.apply_items && a.apply_items <= (int)gridDim.x &&
+               a.sh.kpad * first_tile.count <= kGU * NT;
+        if (ov_a) {
+            ai::apply_tc_setup<MODE>(a.ap, a.sh, first_tile, ts, base, offs);
+            ai::gather_rows_pz_load<MODE, kGU>(a.ap.pz, a.ap.m, first_tile.count, base, offs,
+                                              a.sh.kpad * a.sh.esz / 16, gw);
+        }
+    }
     unsigned long long t_prev = (a.timers && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
     unsigned long long t_acc[4] = {0, 0, 0, 0};
     for (int loop = 0; loop < a.max_loops; ++loop) {
         // ---- phase A: element products
         bool failed = false;
         ArrayCursor curA{solo ? 0 : -1, 0};   // two-phase iteration: groups done per array (alpha fold)
-        for (int w = blockIdx.x; w < a.apply_items; w += gridDim.x) {
+        if constexpr (AM == AM_TC) {
+            if (ov_a && s_active) {   // the tile's loads are in gw: the direction update, then the products
+                ai::gather_rows_pz_store<MODE, kGU>(gw, (float)s_beta, a.ap.m, first_tile.count,
+                                                    a.sh.kpad * a.sh.esz / 16, ts.sA, a.sh.a_plane,
+                                                    tc::sbo_bytes(a.sh.kpad, a.sh.esz), ts.sP, ts.ldp);
+                failed = !ai::apply_tc_finish<MODE>(a.ap, a.sh, first_tile, ts);
+            }
+        }
+        for (int w = blockIdx.x; w < a.apply_items && !ov_a; w += gridDim.x) {
             if constexpr (AM == AM_TC) {
                 const ApplyWork it = w == (int)blockIdx.x ? first_tile : a.ap.work[w];
                 if (!solo && it.array != curA.k) switch_array(curA, it.array, 3);
@@ -514,6 +541,11 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         }   // three-phase iteration
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, FUSED ? 1 : 2, t_prev, t_acc);
+        if constexpr (AM == AM_TC) {
+            if (ov_a && s_active)   // the next phase A's loads in flight during the beta fold
+                ai::gather_rows_pz_load<MODE, kGU>(a.ap.pz, a.ap.m, first_tile.count, base, offs,
+                                                  a.sh.kpad * a.sh.esz / 16, gw);
+        }
         if (solo && s_active) {
             double rz, rr;
             pi::cta_fold8_2(a.part_rz + s_A.vwork_off, a.part_rr + s_A.vwork_off, s_A.n_vwork, sh8, rz, rr);
