@@ -37,9 +37,7 @@ ORACLE_SIDE = 40          # bounded CPU sample: a 40x40 array of the same block
 # 100x100 solve divided by its PCG iterations (bytes per iteration), by
 # precision mode; a mode is absent until it has been measured on the current
 # kernel (the figure is then reported as null).
-# BF16X3 (mode 3): about 31.6 MB read + written by the 4 launches of one solve
-# (7.6 MB of model data read per launch) over its 304 iterations.
-PCG_TRAFFIC: dict[int, float] = {3: 104000.0}
+PCG_TRAFFIC: dict[int, float] = {}
 
 
 def parse():

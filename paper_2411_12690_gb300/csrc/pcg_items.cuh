@@ -358,47 +358,69 @@ __device__ __forceinline__ void isum_update_item_pz(const VecWork& it, const Arr
     }
 }
 
+// resident_update_item_pz in two halves: the loads of one round (U DOFs per
+// thread: the pair and the owners' element products summed in fixed order),
+// which need neither alpha nor beta, and the update itself. Between them the
+// caller may fold alpha while the loads are in flight.
+template <int U>
+__device__ __forceinline__ void resident_update_load(long long start, int count, int l0,
+                                                     const int* __restrict__ soff, int stride,
+                                                     const float* __restrict__ Y, const float2* __restrict__ pz,
+                                                     float (&s)[U], float2 (&pzv)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int l = l0 + u * (int)blockDim.x;
+        s[u] = 0.f;
+        pzv[u] = make_float2(0.f, 0.f);
+        if (l < count) {
+            pzv[u] = pz[start + l];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int off = soff[c * stride + l];
+                if (off >= 0) s[u] += __ldcg(Y + off);
+            }
+        }
+    }
+}
+
+template <int U>
+__device__ __forceinline__ void resident_update_finish(long long start, int count, int l0, const float* sd, float* sx,
+                                                       float* sr, float2* __restrict__ pz, const float (&s)[U],
+                                                       const float2 (&pzv)[U], float beta, float al,
+                                                       DotAcc<float>& srz, DotAcc<float>& srr) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int l = l0 + u * (int)blockDim.x;
+        if (l < count) {
+            const float dv = sd[l];
+            const float qv = dv != 0.f ? s[u] : 0.f;
+            const float pn = p_next(pzv[u].y, pzv[u].x, beta);
+            const float rn = fmaf(-al, qv, sr[l]);
+            const float zn = dv * rn;
+            pz[start + l] = make_float2(pn, zn);
+            sx[l] = fmaf(al, pn, sx[l]);
+            sr[l] = rn;
+            srz.add(rn, zn);
+            srr.add(rn, rn);
+        }
+    }
+}
+
+constexpr int kResidentU = 5;   // DOFs per thread per round of the resident update
+
 __device__ __forceinline__ void resident_update_item_pz(long long start, int count, const int* __restrict__ soff,
                                                         int stride, const float* sd, float* sx, float* sr,
                                                         const float* __restrict__ Y, float2* __restrict__ pz,
                                                         float beta, float al, DotAcc<float>& srz,
                                                         DotAcc<float>& srr) {
-    constexpr int U = 5;
+    constexpr int U = kResidentU;
     srz = DotAcc<float>();
     srr = DotAcc<float>();
     for (int l0 = threadIdx.x; l0 < count; l0 += (int)blockDim.x * U) {
         float s[U];
         float2 pzv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int l = l0 + u * (int)blockDim.x;
-            s[u] = 0.f;
-            pzv[u] = make_float2(0.f, 0.f);
-            if (l < count) {
-                pzv[u] = pz[start + l];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int off = soff[c * stride + l];
-                    if (off >= 0) s[u] += __ldcg(Y + off);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int l = l0 + u * (int)blockDim.x;
-            if (l < count) {
-                const float dv = sd[l];
-                const float qv = dv != 0.f ? s[u] : 0.f;
-                const float pn = p_next(pzv[u].y, pzv[u].x, beta);
-                const float rn = fmaf(-al, qv, sr[l]);
-                const float zn = dv * rn;
-                pz[start + l] = make_float2(pn, zn);
-                sx[l] = fmaf(al, pn, sx[l]);
-                sr[l] = rn;
-                srz.add(rn, zn);
-                srr.add(rn, rn);
-            }
-        }
+        resident_update_load<U>(start, count, l0, soff, stride, Y, pz, s, pzv);
+        resident_update_finish<U>(start, count, l0, sd, sx, sr, pz, s, pzv, beta, al, srz, srr);
     }
 }
 

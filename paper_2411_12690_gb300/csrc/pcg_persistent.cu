@@ -150,7 +150,10 @@ struct ArrayCursor {
     int k, count;   // array, items done by this CTA in this phase run
 };
 
-template <class V, int AM, int MODE, int RPT, int NT, int MINB>
+// RES: compiled for one array on resident vector slices only (the host checks
+// the conditions: one array, a.resident, n_vwork no larger than the grid), so
+// that the batch paths do not count against this variant's registers.
+template <class V, int AM, int MODE, int RPT, int NT, int MINB, bool RES = false>
 __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArgs a) {
     extern __shared__ uint8_t smraw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     // CTA 0 writes the rest of the state for the host. (Not compiled for the
     // streamed tensor-core apply, whose registers are fully used and whose
     // workloads are batches.)
-    const bool solo = AM != AM_TCS && a.n_arrays == 1;
+    const bool solo = RES || (AM != AM_TCS && a.n_arrays == 1);
     if constexpr (AM == AM_TC) {
         if (solo) {   // one array: its descriptor and beta come from this CTA's shared copies
             ts.A_pre = &s_A;
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     // work item per CTA): the CTA's item never changes during the solve, so its
     // x, r, D^-1 and owner offsets live in shared memory (after the tensor-core
     // buffers) and only p and z go through global memory.
-    const bool resident = FUSED && solo && a.resident && a.n_vwork <= (int)gridDim.x;
+    const bool resident = RES || (FUSED && solo && a.resident && a.n_vwork <= (int)gridDim.x);
     V *sVd = nullptr, *sVx = nullptr, *sVr = nullptr;
     int* sOff = nullptr;
     long long v_start = 0;
@@ -348,19 +351,23 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
     __syncthreads();
     // the CTA's first tile, read once (every iteration starts with it)
     const ApplyWork first_tile = (AM == AM_TC && (int)blockIdx.x < a.apply_items) ? a.ap.work[blockIdx.x] : ApplyWork{};
-    // The beta fold overlapped with the next gather's loads (one array,
-    // resident slices, the CTA's only tile gathered in one round): the (p, z)
-    // loads, which do not need beta, are issued right after the barrier that
-    // precedes the fold, and the direction update p = z + beta p follows it --
-    // the same operations in the same order as without the overlap. (The same
-    // for the alpha fold and the vector phase's loads was measured slower: the
-    // registers the loads hold across the fold push the kernel into spills.)
+    // Folds overlapped with loads (the RES variant: one array, resident
+    // slices): the loads that do not need a fold's result are issued right
+    // after the barrier that precedes the fold, and the arithmetic that needs
+    // it follows the fold -- the next gather's (p, z) loads before the beta
+    // fold (ov_a: the CTA's only tile, gathered in one round), the element
+    // products and pairs of the CTA's slice before the alpha fold (ov_b: one
+    // round). The same operations in the same order as without the overlap.
     constexpr int kGU = 12;
-    bool ov_a = false;
+    constexpr int kRU = pi::kResidentU;
+    bool ov_a = false, ov_b = false;
     float2 gw[kGU];
-    if constexpr (AM == AM_TC) {
-        ov_a = resident && a.ap.pz && (int)blockIdx.x < a.apply_items && a.apply_items <= (int)gridDim.x &&
+    float rs[kRU];
+    float2 rpz[kRU];
+    if constexpr (AM == AM_TC && RES) {
+        ov_a = a.ap.pz && (int)blockIdx.x < a.apply_items && a.apply_items <= (int)gridDim.x &&
                a.sh.kpad * first_tile.count <= kGU * NT;
+        ov_b = (int)blockIdx.x < a.n_vwork && v_count <= kRU * NT;
         if (ov_a) {
             ai::apply_tc_setup<MODE>(a.ap, a.sh, first_tile, ts, base, offs);
             ai::gather_rows_pz_load<MODE, kGU>(a.ap.pz, a.ap.m, first_tile.count, base, offs,
@@ -418,6 +425,9 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
         if (!grid_sync(a, &s_ok, &s_kbar)) break;
         phase_mark(a, 0, t_prev, t_acc);
         if constexpr (FUSED) {
+            if (ov_b && s_active)   // the slice's loads in flight during the alpha fold
+                pi::resident_update_load<kRU>(v_start, v_count, tid, sOff, kVecChunkTC,
+                                              static_cast<const float*>(a.ap.Y), a.ap.pz, rs, rpz);
             // ---- alpha from the group sums of p_e^T Y_e (one array: every CTA folds)
             if (solo && s_active) {
                 const double pq = pi::cta_fold8(a.ap.gpart + s_A.grp_off, s_A.n_grp, sh8);
@@ -446,9 +456,14 @@ __global__ void __launch_bounds__(NT, MINB) k_pcg(const __grid_constant__ PcgArg
             if (resident) {
                 if ((int)blockIdx.x < a.n_vwork && s_active) {
                     pi::DotAcc<float> srz, srr;
-                    pi::resident_update_item_pz(v_start, v_count, sOff, kVecChunkTC, sVd, sVx, sVr,
-                                                static_cast<const float*>(a.ap.Y), const_cast<float2*>(a.ap.pz),
-                                                (float)s_scalar2, (float)s_scalar, srz, srr);
+                    if (ov_b)
+                        pi::resident_update_finish<kRU>(v_start, v_count, tid, sVd, sVx, sVr,
+                                                        const_cast<float2*>(a.ap.pz), rs, rpz, (float)s_scalar2,
+                                                        (float)s_scalar, srz, srr);
+                    else
+                        pi::resident_update_item_pz(v_start, v_count, sOff, kVecChunkTC, sVd, sVx, sVr,
+                                                    static_cast<const float*>(a.ap.Y), const_cast<float2*>(a.ap.pz),
+                                                    (float)s_scalar2, (float)s_scalar, srz, srr);
                     double rz, rr;
                     pi::block_sum2(srz, srr, shr, rz, rr);
                     if (tid == 0) {
@@ -715,6 +730,19 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
             smem += vec_smem;
         }
         const int need = std::max(a.apply_items, vneed);
+        // one array whose vector items fit one per SM: the variant compiled for it alone (every
+        // cooperative grid has at least one CTA per SM, so each CTA keeps at most one item)
+        if (a.resident && s->n_vwork <= s->ctx->num_sms) {
+            switch (prec) {
+                case MSTRESS_TF32:
+                    return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1, true>, s, a, smem, need, 128);
+                case MSTRESS_BF16:
+                    return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16, 0, 512, 1, true>, s, a, smem, need, 128);
+                default:
+                    return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_BF16X3, 0, 512, 1, true>, s, a, smem, need,
+                                            128);
+            }
+        }
         switch (prec) {
             case MSTRESS_TF32:
                 return launch_coop<512>(k_pcg<float, AM_TC, MSTRESS_TF32, 0, 512, 1>, s, a, smem, need, 128);
