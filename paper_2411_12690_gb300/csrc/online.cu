@@ -675,15 +675,20 @@ void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
 
 // FP64 residual r = b - A x (a5) and the outer stopping test; returns whether
 // any array still needs a refinement step. Y must be an FP64 element buffer.
-bool outer_check(mstress_sol_s* s, void* Y64, int max_outer) {
+bool outer_check(mstress_sol_s* s, void* Y64, int max_outer, bool x_zero) {
     cudaStream_t stream = s->ctx->stream;
     PcgVectors& v = s->v64;
-    launch_apply(s, MSTRESS_FP64, v.x.ptr, nullptr, false, nullptr, Y64);
-    launch_isum(s, Y64, false, v.x.ptr, nullptr, v.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
-    VecArgs va = vec_args(s, v);
-    va.rhs = s->b.ptr;
-    k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
-    MS_LAUNCH_CHECK();
+    if (!x_zero) {
+        launch_apply(s, MSTRESS_FP64, v.x.ptr, nullptr, false, nullptr, Y64);
+        launch_isum(s, Y64, false, v.x.ptr, nullptr, v.q.ptr, false, s->dinv.as<double>(), nullptr, nullptr);
+        VecArgs va = vec_args(s, v);
+        va.rhs = s->b.ptr;
+        k_residual<<<grid_for(s, s->n_vwork, 8), kThreads, 0, stream>>>(va);
+        MS_LAUNCH_CHECK();
+    }
+    // x_zero: x = 0 since refine_start, whose start kernel left r = b on the free DOFs
+    // and its <r, r> partials, in the same loop and order k_residual uses
+    // (b - 0 = b): nothing to recompute
     ScalarArgs sa = scalar_args(s, v, 2, s->ctx->opts.rtol, max_outer, nullptr);
     k_scalars<<<1, 1024, 0, stream>>>(sa);
     MS_LAUNCH_CHECK();
@@ -1053,7 +1058,7 @@ void refine_start(mstress_sol_s* s) {
 }
 
 // a5: FP64 residual and stopping test; true if any array takes another step.
-bool refine_check(mstress_sol_s* s) { return outer_check(s, s->Y64, s->ctx->opts.max_outer); }
+bool refine_check(mstress_sol_s* s, bool x_zero) { return outer_check(s, s->Y64, s->ctx->opts.max_outer, x_zero); }
 
 // Relative tolerance of an inner (reduced-precision) solve: the option, or,
 // when it is 0, a per-precision value near the reduction one refinement step
@@ -1169,7 +1174,7 @@ void run_solve(mstress_sol_s* s) {
     refine_start(s);
     bool checked = false;
     for (int k = 0; k <= o.max_outer; ++k) {
-        if (!refine_check(s)) {
+        if (!refine_check(s, k == 0)) {
             checked = true;
             break;
         }

@@ -192,7 +192,7 @@ struct LayoutIn {
 void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in);
 void solve_prepare(mstress_sol_s* s);
 void refine_start(mstress_sol_s* s);
-bool refine_check(mstress_sol_s* s);
+bool refine_check(mstress_sol_s* s, bool x_zero = false);   // x_zero: the first check after refine_start
 void refine_inner(mstress_sol_s* s);
 void solve_finish(mstress_sol_s* s, bool refined, bool checked);
 void check_device_error(mstress_sol_s* s);
