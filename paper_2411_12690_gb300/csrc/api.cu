@@ -228,6 +228,7 @@ void mstress_free_ctx(mstress_ctx ctx) {
     ctx->allocs.clear();
     ctx->trim(0);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
+    if (ctx->h_states) cudaFreeHost(ctx->h_states);
     delete ctx;
 }
 

@@ -145,6 +145,10 @@ struct mstress_ctx_s {
     std::string last_error;
     // pinned host words for polling device flags
     int* h_flag = nullptr;
+    // pinned host copy of the inner solves' per-array states (iteration counts),
+    // read at the next stream synchronisation of the solve
+    void* h_states = nullptr;
+    size_t h_states_bytes = 0;
 
     void* alloc(size_t bytes);
     void release(void* p);

@@ -640,13 +640,9 @@ void pcg_run(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter) {
     // preferred: one persistent cooperative launch for the whole run, except
     // for large batches on the streamed apply (per-phase launches, same bits)
     const bool wide = std::is_same<V, float>::value && pcg_wide(s, prec);
-    if (!wide && pcg_run_persistent(s, v, prec, max_iter, std::is_same<V, float>::value)) {
-        MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
-        MS_CUDA(cudaStreamSynchronize(stream));
-        MS_REQUIRE(s->ctx->h_flag[2] == 0, MSTRESS_EDEVICE_TIMEOUT,
-                   "a tensor-core wait or a grid barrier timed out on the device");
-        return;
-    }
+    // (no synchronisation: a wait that expired is reported by the next check of the
+    // device error word, in the refinement check or at the end of the solve)
+    if (!wide && pcg_run_persistent(s, v, prec, max_iter, std::is_same<V, float>::value)) return;
     if (stream != nullptr && !s->graph[gi] && !s->no_while[gi]) s->no_while[gi] = !build_while_graph<V>(s, v, prec, gi, max_iter);
     if (s->graph[gi]) {
         MS_CUDA(cudaGraphLaunch(s->graph[gi], stream));
@@ -692,8 +688,11 @@ bool outer_check(mstress_sol_s* s, void* Y64, int max_outer, bool x_zero) {
     ScalarArgs sa = scalar_args(s, v, 2, s->ctx->opts.rtol, max_outer, nullptr);
     k_scalars<<<1, 1024, 0, stream>>>(sa);
     MS_LAUNCH_CHECK();
-    MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(cudaMemcpyAsync(s->ctx->h_flag, s->flag.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
     MS_CUDA(cudaStreamSynchronize(stream));
+    flush_inner_iters(s);
+    MS_REQUIRE(s->ctx->h_flag[2] == 0, MSTRESS_EDEVICE_TIMEOUT,
+               "a tensor-core wait or a grid barrier timed out on the device");
     return s->ctx->h_flag[0] != 0;
 }
 
@@ -910,6 +909,8 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
 }
 
 void check_device_error(mstress_sol_s* s) {
+    MS_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    flush_inner_iters(s);
     int f[4];
     MS_CUDA(cudaMemcpy(f, s->flag.ptr, sizeof(f), cudaMemcpyDeviceToHost));
     MS_REQUIRE(f[2] == 0, MSTRESS_EDEVICE_TIMEOUT, "a tensor-core wait or a grid barrier timed out on the device");
@@ -1097,11 +1098,25 @@ void refine_inner(mstress_sol_s* s) {
             s->d_vwork.as<VecWork>(), s->n_vwork, gate, s->v64.x.as<double>(), vi.x.as<float>());
     }
     MS_LAUNCH_CHECK();
-    std::vector<PcgState> inner(s->n_arrays);
-    MS_CUDA(cudaMemcpyAsync(inner.data(), vi.state.ptr, inner.size() * sizeof(PcgState), cudaMemcpyDeviceToHost,
-                            stream));
-    MS_CUDA(cudaStreamSynchronize(stream));
+    // the iteration counts come back with the next synchronisation (flush_inner_iters)
+    mstress_ctx ctx = s->ctx;
+    const size_t bytes = (size_t)s->n_arrays * sizeof(PcgState);
+    if (ctx->h_states_bytes < bytes) {
+        if (ctx->h_states) MS_CUDA(cudaFreeHost(ctx->h_states));
+        ctx->h_states = nullptr;
+        ctx->h_states_bytes = 0;
+        MS_CUDA(cudaHostAlloc(&ctx->h_states, bytes, cudaHostAllocDefault));
+        ctx->h_states_bytes = bytes;
+    }
+    MS_CUDA(cudaMemcpyAsync(ctx->h_states, vi.state.ptr, bytes, cudaMemcpyDeviceToHost, stream));
+    s->inner_pending = true;
+}
+
+void flush_inner_iters(mstress_sol_s* s) {
+    if (!s->inner_pending) return;
+    const PcgState* inner = static_cast<const PcgState*>(s->ctx->h_states);
     for (int a = 0; a < s->n_arrays; ++a) s->results[a].iters += inner[a].iters;
+    s->inner_pending = false;
 }
 
 // True FP64 residual of the final iterate, per-array results, and the

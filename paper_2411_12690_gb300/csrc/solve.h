@@ -155,6 +155,8 @@ struct mstress_sol_s {
     ms::PcgVectors v64, v32;              // FP64 outer / plain vectors, FP32 inner vectors
     ms::PcgVectors v64i;                  // FP64 inner vectors (refinement with an FP64 inner solve)
     bool inner64 = false;                 // refinement steps solve the correction in FP64
+    bool inner_pending = false;           // the last inner solve's states are on their way to
+                                          // ctx->h_states (see flush_inner_iters)
     ms::DBuf Y64own;                      // FP64 element buffer of the mixed modes
     void* Y64 = nullptr;                  // FP64 element products (Y64own, or Y in FP64 mode)
     ms::DBuf Y;                           // element-by-element products [block][ldY]
@@ -193,6 +195,7 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in);
 void solve_prepare(mstress_sol_s* s);
 void refine_start(mstress_sol_s* s);
 bool refine_check(mstress_sol_s* s, bool x_zero = false);   // x_zero: the first check after refine_start
+void flush_inner_iters(mstress_sol_s* s);   // after a stream synchronisation: add the inner iterations
 void refine_inner(mstress_sol_s* s);
 void solve_finish(mstress_sol_s* s, bool refined, bool checked);
 void check_device_error(mstress_sol_s* s);
