@@ -229,6 +229,7 @@ void mstress_free_ctx(mstress_ctx ctx) {
     ctx->trim(0);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
     if (ctx->h_states) cudaFreeHost(ctx->h_states);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     delete ctx;
 }
 

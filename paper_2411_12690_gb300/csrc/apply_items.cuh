@@ -491,22 +491,22 @@ __device__ __forceinline__ bool apply_tc_finish(const ApplyArgs& a, const TcShap
     }
     if (dots) {
         // one partial per 8-block group of the tile: each block's column
-        // chunks summed in order, then the group's blocks in order
-        // (independent of the tile size)
+        // chunks summed in order (thread b of warps 0..3), then the group's
+        // blocks in order by the first of its 8 lanes (independent of the
+        // tile size)
         __syncthreads();
-        const int nch = sh.npad >> 4;
-        if (tid < it.count) {
+        if (tid < kTileTC) {
+            const int nch = sh.npad >> 4;
             double sb = 0;
-            for (int c = 0; c < nch; ++c) sb += ts.sDot[c * kTileTC + tid];
-            ts.sDot[tid] = sb;   // chunk 0's slot of this block, read only by this thread above
-        }
-        __syncthreads();
-        const int ng = (it.count + 7) >> 3;
-        if (tid < ng) {
+            if (tid < it.count)
+                for (int c = 0; c < nch; ++c) sb += ts.sDot[c * kTileTC + tid];
             double sum = 0;
-            const int b1 = min(8 * tid + 8, it.count);
-            for (int bb = 8 * tid; bb < b1; ++bb) sum += ts.sDot[bb];
-            a.gpart[it.grp + tid] = sum;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const double v = __shfl_sync(0xffffffffu, sb, (lane & ~7) + j);
+                if ((tid & ~7) + j < it.count) sum += v;
+            }
+            if ((lane & 7) == 0 && tid < it.count) a.gpart[it.grp + (tid >> 3)] = sum;
         }
     }
     tc::fence_before();

@@ -149,6 +149,10 @@ struct mstress_ctx_s {
     // read at the next stream synchronisation of the solve
     void* h_states = nullptr;
     size_t h_states_bytes = 0;
+    // pinned host staging of a solve's work lists on their way to the device
+    // (reused: a solve's set-up copies finish before the next set-up starts)
+    uint8_t* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
 
     void* alloc(size_t bytes);
     void release(void* p);

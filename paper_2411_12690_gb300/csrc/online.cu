@@ -847,9 +847,31 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
     s->h_awork_rec = awork_rec;
 
     cudaStream_t st = ctx->stream;
+    // the work lists go through one pinned staging buffer, so that their copies
+    // are asynchronous (the stream's earlier work, which may still read the
+    // staging buffer of a previous set-up, is waited for first)
+    {
+        const size_t need = sizeof(LocalMap) + s->arrays.size() * sizeof(ArrayDev) + bref.size() * sizeof(BlockRef) +
+                            blist.size() * sizeof(int) +
+                            (awork.size() + awork_tc.size() + awork_rec.size()) * sizeof(ApplyWork) +
+                            vwork.size() * sizeof(VecWork) + s->site.size() + fixed.size() +
+                            xbc.size() * sizeof(double) + 16 * 64;
+        MS_CUDA(cudaStreamSynchronize(st));
+        if (ctx->h_stage_bytes < need) {
+            if (ctx->h_stage) MS_CUDA(cudaFreeHost(ctx->h_stage));
+            ctx->h_stage = nullptr;
+            ctx->h_stage_bytes = 0;
+            MS_CUDA(cudaHostAlloc((void**)&ctx->h_stage, need, cudaHostAllocDefault));
+            ctx->h_stage_bytes = need;
+        }
+    }
+    size_t stage_off = 0;
     auto up = [&](DBuf& d, const void* src, size_t bytes) {
         alloc_into(ctx, d, bytes, false);
-        MS_CUDA(cudaMemcpyAsync(d.ptr, src, bytes, cudaMemcpyHostToDevice, st));
+        if (bytes == 0) return;
+        std::memcpy(ctx->h_stage + stage_off, src, bytes);
+        MS_CUDA(cudaMemcpyAsync(d.ptr, ctx->h_stage + stage_off, bytes, cudaMemcpyHostToDevice, st));
+        stage_off += (bytes + 63) / 64 * 64;
     };
     up(s->d_lm, &lm, sizeof(LocalMap));
     up(s->d_arrays, s->arrays.data(), s->arrays.size() * sizeof(ArrayDev));
