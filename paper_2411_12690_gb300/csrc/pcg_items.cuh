@@ -195,7 +195,9 @@ __device__ __forceinline__ void for_owners(const ArrayDev& A, const int16_t* __r
 // of U * blockDim.x DOFs costs one round trip to L2 instead of a chain of
 // dependent ones. The owner candidates are visited rows ascending then columns
 // ascending, as in for_owners; constrained rows are zeroed after the sum.
-template <int U, class V, class YT>
+// NC: nothing writes Y during the kernel (a kernel of its own), so the
+// owners' element products may come through L1 (ld.global.nc).
+template <int U, class V, class YT, bool NC = false>
 __device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev& A, const LocalMap* lm, const V* dinv, int ldY,
                                        const YT* __restrict__ Y, V* __restrict__ p, const V* __restrict__ z,
                                        V* __restrict__ q, V beta) {
@@ -228,8 +230,10 @@ __device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev
                     const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
                     if (use) {
                         const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
-                        if (sidx >= 0)
-                            s[u] += (V)__ldcg(Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp);
+                        if (sidx >= 0) {
+                            const YT* yp = Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp;
+                            s[u] += (V)(NC ? __ldg(yp) : __ldcg(yp));
+                        }
                     }
                 }
             }

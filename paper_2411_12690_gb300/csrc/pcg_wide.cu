@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kWT, 2) k_w_isum(const __grid_constant__ WideA
         wide_switch(a, c, it.array, false, sA, s_active, s_beta);
         if (!s_active) continue;
         const pi::DotAcc<float> acc =
-            pi::isum_item<4, float, float>(it, sA, a.lm, a.dinv, a.ldY, a.Y, a.p, a.z, a.q, (float)s_beta);
+            pi::isum_item<4, float, float, true>(it, sA, a.lm, a.dinv, a.ldY, a.Y, a.p, a.z, a.q, (float)s_beta);
         const double t = pi::block_sum(acc, shr);
         if (threadIdx.x == 0) a.part_pq[w] = t;
     }
