@@ -308,6 +308,38 @@ void mstress_free_server(mstress_server srv);
    timeout path (no fault, no trap; every wait stays bounded). */
 int mstress_set_wait_limit(mstress_ctx ctx, int64_t limit_ns, int withhold_next);
 
+/* Row-strip partition of one array's global stage (section 4.3, Eq. 20) over
+   `world` ranks: the plan of a solve split by block rows, in which each rank
+   applies K_r to its own blocks, the lattice row on each strip boundary is
+   summed across the two ranks whose blocks touch it, and the PCG scalars are
+   summed over ranks. Host arithmetic only (no device call).
+   For an array of ny block rows and basis order `order` (n = order + 1
+   Lagrange nodes per axis, so block row j spans lattice rows j (n-1) ..
+   (j+1)(n-1)), rank `rank` gets:
+     j0, j1     its block rows [j0, j1): ny rows split as evenly as possible,
+                lower ranks taking the extra rows;
+     y_own0, y_own1  the lattice rows it owns, [y_own0, y_own1): from j0 (n-1)
+                up to but excluding j1 (n-1), the last rank also the top row
+                ny (n-1); every lattice row has exactly one owner;
+     y_send     j1 (n-1), the row its blocks touch that rank + 1 owns: its
+                partial interface sums there go to rank + 1, and rank + 1's
+                values of the vector being applied there come back before each
+                apply (-1 on the last rank);
+     y_recv     j0 (n-1), the owned row for which it receives rank - 1's
+                partial sums and to which it sends its values (-1 on rank 0);
+     prev, next the neighbouring ranks (-1 where there is none).
+   Returns MSTRESS_EINVAL for a NULL out, ny < 1, order outside [1, 7],
+   world < 1, rank outside [0, world) or world > ny (every strip needs a block
+   row). */
+typedef struct {
+    int j0, j1;
+    int y_own0, y_own1;
+    int y_send, y_recv;
+    int prev, next;
+} mstress_strip;
+
+int mstress_strip_partition(int ny, int order, int world, int rank, mstress_strip* out);
+
 /* Number of CUDA kernels this library has launched in this process (a graph
    replay counts its kernel nodes). For accounting in benchmarks. */
 int mstress_launch_count(int64_t* n);

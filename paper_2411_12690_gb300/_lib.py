@@ -72,6 +72,11 @@ class mstress_bc(C.Structure):
                 ("n_prescribed", C.c_size_t)]
 
 
+class mstress_strip(C.Structure):
+    _fields_ = [("j0", C.c_int), ("j1", C.c_int), ("y_own0", C.c_int), ("y_own1", C.c_int),
+                ("y_send", C.c_int), ("y_recv", C.c_int), ("prev", C.c_int), ("next", C.c_int)]
+
+
 class mstress_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
                 ("inner_rtol", C.c_double), ("max_outer", C.c_int), ("hbm_budget", C.c_size_t),
@@ -112,6 +117,7 @@ SIGNATURES = {
     "mstress_apply": (I, [P, C.POINTER(mstress_layout), P, P, I]),
     "mstress_launch_count": (I, [C.POINTER(C.c_int64)]),
     "mstress_set_wait_limit": (I, [P, C.c_int64, I]),
+    "mstress_strip_partition": (I, [I, I, I, I, C.POINTER(mstress_strip)]),
     "mstress_profile": (I, [P, P, I, I, PD]),
     "mstress_apply_noalloc": (I, [P, I, I, P, P, P]),
     "mstress_sol_phase_ms": (I, [P, PD]),

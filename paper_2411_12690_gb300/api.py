@@ -348,6 +348,19 @@ def launch_count() -> int:
     return n.value
 
 
+def strip_partition(ny: int, order: int, world: int, rank: int) -> dict:
+    """Row-strip plan of one array's global stage for `rank` of `world`
+    (mstress_strip_partition): block rows [j0, j1), owned lattice rows
+    [y_own0, y_own1), the boundary rows sent (y_send) and received (y_recv),
+    and the neighbouring ranks (-1 where none)."""
+    lib = L.load()
+    out = L.mstress_strip()
+    rc = lib.mstress_strip_partition(ny, order, world, rank, C.byref(out))
+    if rc != L.MSTRESS_OK:
+        raise MstressError(rc, "invalid strip partition arguments")
+    return {name: getattr(out, name) for name, _ in L.mstress_strip._fields_}
+
+
 def profile(ctx: Context, sol: Solution, phase: int, reps: int = 20) -> float:
     """Mean duration (ms) of one launch of a solve phase kernel (see mstress_profile)."""
     ms = C.c_double()

@@ -233,6 +233,25 @@ void mstress_free_ctx(mstress_ctx ctx) {
     delete ctx;
 }
 
+int mstress_strip_partition(int ny, int order, int world, int rank, mstress_strip* out) {
+    if (!out || ny < 1 || order < 1 || order > 7 || world < 1 || rank < 0 || rank >= world || world > ny)
+        return MSTRESS_EINVAL;
+    const int n1 = order;   // lattice rows per block row
+    const int base = ny / world, extra = ny % world;
+    const int j0 = rank * base + std::min(rank, extra);
+    const int j1 = j0 + base + (rank < extra ? 1 : 0);
+    const bool last = rank == world - 1;
+    out->j0 = j0;
+    out->j1 = j1;
+    out->y_own0 = j0 * n1;
+    out->y_own1 = last ? ny * n1 + 1 : j1 * n1;
+    out->y_send = last ? -1 : j1 * n1;
+    out->y_recv = rank == 0 ? -1 : j0 * n1;
+    out->prev = rank == 0 ? -1 : rank - 1;
+    out->next = last ? -1 : rank + 1;
+    return MSTRESS_OK;
+}
+
 const char* mstress_last_error(mstress_ctx ctx) {
     if (!ctx) return "null context";
     return ctx->last_error.c_str();
