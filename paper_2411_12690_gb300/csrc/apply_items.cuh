@@ -38,6 +38,12 @@ __device__ __forceinline__ V gather_nc(const V* x, const V* z, long long g, V be
     return z ? p_next(__ldg(z + g), __ldg(x + g), beta) : __ldg(x + g);
 }
 
+// (p, z) pairs through the read-only path: one 8-byte load per coefficient.
+__device__ __forceinline__ float gather_pz_nc(const float2* pz, long long g, float beta) {
+    const float2 v = __ldg(pz + g);
+    return p_next(v.y, v.x, beta);
+}
+
 // Gather the element DOFs of a tile of (1 << tile_shift) blocks, index
 // idx = k * tile + b, eight values per thread in flight at a time (the loads of
 // a round are independent, so they overlap instead of queueing one L2 round
@@ -616,7 +622,7 @@ struct QuadMap {
 template <int MODE, int QU, bool NC>
 __device__ __forceinline__ void quad_load(const float* __restrict__ x, const float* __restrict__ z, float beta, int m,
                                           int count, const long long* base, const int* offs, int k0, int u0, int nthr,
-                                          float (&v)[QU][4]) {
+                                          float (&v)[QU][4], const float2* pz = nullptr) {
     using QM = QuadMap<MODE>;
 #pragma unroll
     for (int q = 0; q < QU; ++q) {
@@ -634,7 +640,12 @@ __device__ __forceinline__ void quad_load(const float* __restrict__ x, const flo
                 o.z = k + 2 < m ? offs[k + 2] : 0;
             }
         }
-        if constexpr (NC) {
+        if (NC && pz) {
+            v[q][0] = live && k < m ? gather_pz_nc(pz, bb + o.x, beta) : 0.f;
+            v[q][1] = live && k + 1 < m ? gather_pz_nc(pz, bb + o.y, beta) : 0.f;
+            v[q][2] = live && k + 2 < m ? gather_pz_nc(pz, bb + o.z, beta) : 0.f;
+            v[q][3] = live && k + 3 < m ? gather_pz_nc(pz, bb + o.w, beta) : 0.f;
+        } else if constexpr (NC) {
             v[q][0] = live && k < m ? gather_nc(x, z, bb + o.x, beta) : 0.f;
             v[q][1] = live && k + 1 < m ? gather_nc(x, z, bb + o.y, beta) : 0.f;
             v[q][2] = live && k + 2 < m ? gather_nc(x, z, bb + o.z, beta) : 0.f;
@@ -811,17 +822,19 @@ __device__ bool tcs_apply_phase(const ApplyArgs& a, const TcsShape& sh, TcsState
             tile_setup_part(a, it, A, base, offs, gt, kTcsGather);
             named_sync(1, kTcsGather);
             float vc[kTcsQU][4], vn[kTcsQU][4];
-            if (PREFETCH) quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, 0, gt, kTcsGather, vc);
+            if (PREFETCH)
+                quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, 0, gt, kTcsGather, vc, a.pz);
             bool ok = true;
             for (int c = 0; c < sh.nck; ++c, ++g) {
                 const uint32_t slot = g % S, use = g / S;
                 if (!PREFETCH)   // loads issued before the wait for the slot, so they overlap it
-                    quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, c * sh.ck, gt, kTcsGather, vc);
+                    quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, c * sh.ck, gt, kTcsGather, vc,
+                                                a.pz);
                 if (use > 0) ok = tc::mbar_wait(&ts.empty[slot], (use - 1) & 1u, kTries);
                 if (!ok) break;
                 if (PREFETCH && c + 1 < sh.nck)   // next slot's values in flight while this one is stored
                     quad_load<MODE, kTcsQU, NC>(x, z, beta, a.m, it.count, base, offs, (c + 1) * sh.ck, gt, kTcsGather,
-                                            vn);
+                                            vn, a.pz);
                 quad_store<MODE, kTcsQU>(gt, kTcsGather, vc, ts.slots + slot * slot_bytes, sh.a_plane, sbo);
                 tc::fence_smem_async();
                 tc::mbar_arrive(&ts.fullA[slot]);

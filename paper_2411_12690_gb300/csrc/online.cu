@@ -918,7 +918,8 @@ void validate_and_build(mstress_sol_s* s, const std::vector<LayoutIn>& in) {
         alloc_into(ctx, s->v32.p, nv * sizeof(float), false);
         alloc_into(ctx, s->v32.q, nv * sizeof(float), false);
         alloc_into(ctx, s->v32.state, s->n_arrays * sizeof(PcgState));
-        if (s->use_tc && !tc_streamed(s->m)) alloc_into(ctx, s->pz, nv * sizeof(float2), false);
+        if (s->use_tc && (!tc_streamed(s->m) || pcg_wide(s, s->precision)))
+            alloc_into(ctx, s->pz, nv * sizeof(float2), false);
     }
     if (s->inner64) {
         alloc_into(ctx, s->v64i.x, nv * sizeof(double));
@@ -990,10 +991,9 @@ void autotune_tc_tile(mstress_sol_s* s) {
         for (int c : cand) {
             if (c < 8 || c > kTileTC) continue;
             set_tc_tiles(s, c);
-            launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);   // warm-up
+            launch_apply_wide(s, s->precision, nullptr);   // warm-up
             MS_CUDA(cudaEventRecord(e0, st));
-            for (int r = 0; r < 3; ++r)
-                launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);
+            for (int r = 0; r < 3; ++r) launch_apply_wide(s, s->precision, nullptr);
             MS_CUDA(cudaEventRecord(e1, st));
             MS_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
@@ -1368,7 +1368,8 @@ int mstress_profile(mstress_ctx ctx, mstress_sol sol, int phase, int reps, doubl
     auto run = [&]() {
         switch (phase) {
             case 0:   // gathering p and z as an iteration does (p = z + beta p, beta = 0 here)
-                if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);
+                if (mixed && pcg_wide(s, s->precision)) launch_apply_wide(s, s->precision, nullptr);
+                else if (mixed) launch_apply(s, s->precision, s->v32.p.ptr, s->v32.z.ptr, true, nullptr, s->Y.ptr);
                 else launch_apply(s, MSTRESS_FP64, s->v64.p.ptr, s->v64.z.ptr, false, nullptr, s->Y.ptr);
                 break;
             case 1:

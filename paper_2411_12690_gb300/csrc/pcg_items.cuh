@@ -256,6 +256,100 @@ __device__ __forceinline__ DotAcc<V> isum_item(const VecWork& it, const ArrayDev
     return acc;
 }
 
+// isum_item on (p, z) pairs (FP32, the per-phase iteration of large batches):
+// the same arithmetic, p and z read from one pair and the new p written to its
+// first half. NC: Y is read through L1 (nothing writes it during the kernel).
+template <int U, bool NC>
+__device__ __forceinline__ DotAcc<float> isum_item_pz(const VecWork& it, const ArrayDev& A, const LocalMap* lm,
+                                                      const float* dinv, int ldY, const float* __restrict__ Y,
+                                                      float2* __restrict__ pz, float* __restrict__ q, float beta) {
+    const int n = lm->n, n1 = n - 1;
+    const int16_t* __restrict__ surf = lm->surf_idx;
+    const long long end = it.start + it.count;
+    DotAcc<float> acc;
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
+        float s[U], dv[U];
+        float2 pzv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            s[u] = 0.f;
+            dv[u] = 0.f;
+            pzv[u] = make_float2(0.f, 0.f);
+            if (g < end) {
+                dv[u] = dinv[g];
+                pzv[u] = pz[g];
+                int comp, gx, gy, gz;
+                lattice_coords(A, g, comp, gx, gy, gz);
+                const int ih0 = gx / n1, jh0 = gy / n1;
+                const int ih = min(ih0, A.nx - 1), jh = min(jh0, A.ny - 1);
+                const int il = max((gx % n1 == 0) ? ih0 - 1 : ih0, 0), jl = max((gy % n1 == 0) ? jh0 - 1 : jh0, 0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = (c >> 1) ? jh : jl, i = (c & 1) ? ih : il;
+                    const bool use = ((c >> 1) == 0 || jh != jl) && ((c & 1) == 0 || ih != il);
+                    if (use) {
+                        const int sidx = __ldg(surf + (gz * n + (gy - j * n1)) * n + (gx - i * n1));
+                        if (sidx >= 0) {
+                            const float* yp = Y + (A.block_off + (long long)j * A.nx + i) * ldY + 3 * sidx + comp;
+                            s[u] += NC ? __ldg(yp) : __ldcg(yp);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                const float sv = dv[u] != 0.f ? s[u] : 0.f;
+                const float pn = p_next(pzv[u].y, pzv[u].x, beta);
+                reinterpret_cast<float*>(pz)[2 * g] = pn;
+                q[g] = sv;
+                acc.add(pn, sv);
+            }
+        }
+    }
+    return acc;
+}
+
+// vec1_item on (p, z) pairs: p read from the pair, the new z written to its
+// second half; the same arithmetic and order.
+template <int U>
+__device__ __forceinline__ void vec1_item_pz(const VecWork& it, const float* dinv, float al, float* x, float* r,
+                                             float2* pz, const float* q, DotAcc<float>& srz, DotAcc<float>& srr) {
+    srz = DotAcc<float>();
+    srr = DotAcc<float>();
+    const long long end = it.start + it.count;
+    for (long long g0 = it.start + threadIdx.x; g0 < end; g0 += (long long)blockDim.x * U) {
+        float pv[U], qv[U], xv[U], rv0[U], dv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {   // all loads first
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                pv[u] = reinterpret_cast<const float*>(pz)[2 * g];
+                qv[u] = q[g];
+                xv[u] = x[g];
+                rv0[u] = r[g];
+                dv[u] = dinv[g];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + (long long)u * blockDim.x;
+            if (g < end) {
+                x[g] = fma(al, pv[u], xv[u]);
+                const float rv = fma(-al, qv[u], rv0[u]);
+                const float zv = dv[u] * rv;
+                r[g] = rv;
+                reinterpret_cast<float*>(pz)[2 * g + 1] = zv;
+                srz.add(rv, zv);
+                srr.add(rv, rv);
+            }
+        }
+    }
+}
+
 // Resident vector slice: when a CTA keeps one vector work item for a whole
 // solve, the item's x, r and D^-1 stay in shared memory (only this CTA reads
 // or writes them) and the element-product offsets of each DOF's owners are

@@ -9,6 +9,9 @@
 // This path runs the same iteration as separate launches:
 //   apply      the stand-alone streamed tensor-core apply (p = z + beta p
 //              formed in the gather, the same operand bits and products);
+//              p and z are kept as (p, z) pairs, so that it gathers both
+//              with one 8-byte load (the interface sum writes the first half
+//              of a pair, the update the second);
 //   k_w_isum   interface sum q, p stored, <p,q> partial per vector item;
 //   k_w_alpha  one CTA per array: alpha = <r,z> / <p,q> from the partials;
 //   k_w_vec    x += alpha p, r -= alpha q, z = D^-1 r, <r,z>, <r,r> partials;
@@ -35,7 +38,8 @@ struct WideArgs {
     const float* dinv;
     int ldY;
     const float* Y;
-    float *x, *r, *z, *p, *q;
+    float *x, *r, *q;
+    float2* pz;   // (p, z) pairs
     PcgState* st;
     double *part_pq, *part_rz, *part_rr;
     int* flag;   // [0] any active, [1] CTA ticket, [2] device error, [3] loop count, [5] arrays active
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(kWT, 2) k_w_isum(const __grid_constant__ WideA
         wide_switch(a, c, it.array, false, sA, s_active, s_beta);
         if (!s_active) continue;
         const pi::DotAcc<float> acc =
-            pi::isum_item<4, float, float, true>(it, sA, a.lm, a.dinv, a.ldY, a.Y, a.p, a.z, a.q, (float)s_beta);
+            pi::isum_item_pz<4, true>(it, sA, a.lm, a.dinv, a.ldY, a.Y, a.pz, a.q, (float)s_beta);
         const double t = pi::block_sum(acc, shr);
         if (threadIdx.x == 0) a.part_pq[w] = t;
     }
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(kWT, 2) k_w_vec(const __grid_constant__ WideAr
         pi::DotAcc<float> srz, srr;
         // (4 DOFs per thread in flight: each thread still visits its DOFs, and adds
         // their products, in the persistent solver's order)
-        pi::vec1_item<4, float>(it, a.dinv, (float)s_alpha, a.x, a.r, a.z, a.p, a.q, srz, srr);
+        pi::vec1_item_pz<4>(it, a.dinv, (float)s_alpha, a.x, a.r, a.pz, a.q, srz, srr);
         const double rz = pi::block_sum(srz, shr);
         const double rr = pi::block_sum(srr, shr);
         if (threadIdx.x == 0) {
@@ -176,11 +180,18 @@ bool pcg_wide(const mstress_sol_s* s, int prec) {
     return prec != MSTRESS_FP64 && s->use_tc && tc_streamed(s->m) && s->n_blocks >= kWideBlocks;
 }
 
+void launch_apply_wide(mstress_sol_s* s, int prec, const PcgState* st) {
+    MS_REQUIRE(s->pz.ptr, MSTRESS_EINVAL, "per-phase iteration without (p, z) pairs");
+    ApplyArgs a = apply_args(s, s->v32.p.ptr, s->v32.z.ptr, st, s->Y.ptr, true);
+    a.pz = s->pz.as<float2>();
+    launch_apply_tc(s, prec, a);
+}
+
 void pcg_iteration_wide(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond, cudaGraphConditionalHandle cond,
                         int loop_cap) {
     cudaStream_t stream = s->ctx->stream;
     PcgState* st = v.state.as<PcgState>();
-    launch_apply(s, prec, v.p.ptr, v.z.ptr, true, st, s->Y.ptr);   // gathers p = z + beta p
+    launch_apply_wide(s, prec, st);   // gathers p = z + beta p from the pairs
     WideArgs a;
     std::memset(&a, 0, sizeof(a));
     a.vwork = s->d_vwork.as<VecWork>();
@@ -192,9 +203,8 @@ void pcg_iteration_wide(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond,
     a.Y = s->Y.as<float>();
     a.x = v.x.as<float>();
     a.r = v.r.as<float>();
-    a.z = v.z.as<float>();
-    a.p = v.p.as<float>();
     a.q = v.q.as<float>();
+    a.pz = s->pz.as<float2>();
     a.st = st;
     a.part_pq = s->part.as<double>();
     a.part_rz = a.part_pq + s->n_vwork;

@@ -217,6 +217,7 @@ bool pcg_run_persistent(mstress_sol_s* s, PcgVectors& v, int prec, int max_iter,
 // occupancy of separate kernels does)
 constexpr int64_t kWideBlocks = 4096;
 bool pcg_wide(const mstress_sol_s* s, int prec);
+void launch_apply_wide(mstress_sol_s* s, int prec, const PcgState* st);   // its apply (st null: beta = 0)
 void pcg_iteration_wide(mstress_sol_s* s, PcgVectors& v, int prec, int use_cond, cudaGraphConditionalHandle cond,
                         int loop_cap);
 
