@@ -4,10 +4,10 @@ on CPU ranks over gloo.
 * The plan: for every array height and rank count, the block rows and the
   owned lattice rows of the ranks tile the array exactly once, and each
   rank's boundary row is the next rank's first owned row.
-* The data path on two gloo ranks: a Jacobi-PCG of the reduced system
-  (section 4.3, Eq. 20) on a 6 x 8 array, each rank applying K_r to its own
-  block rows only (the oracle's reduced block models); per iteration the
-  direction's values on the boundary row go from its owner to the rank below
+* The data path on two and three gloo ranks: a Jacobi-PCG of the reduced
+  system (section 4.3, Eq. 20) on a 6 x 8 array, each rank applying K_r to its
+  own block rows only (the oracle's reduced block models); per iteration the
+  direction's values on each boundary row go from its owner to the rank below
   (halo), the partial interface sums there go back up and are added, and
   <p,q>, <r,z>, <r,r> are summed over the ranks. The solution equals the same
   iteration on one rank to 1e-12 and the oracle's direct solve to 1e-9.
@@ -188,14 +188,14 @@ def _rank_main(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_two_rank_strip_solve_equals_one_rank_and_oracle(api):
+@pytest.mark.parametrize("world", [2, 3])
+def test_strip_solve_equals_one_rank_and_oracle(api, world):
     import warnings
     warnings.simplefilter("ignore")
     import torch.multiprocessing as mp
     from cases import SMALL_MESH, oracle_pair
     from oracle import mor
     from paper_2411_12690_gb300 import workloads as W
-    world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -218,8 +218,9 @@ def test_two_rank_strip_solve_equals_one_rank_and_oracle(api):
     one = api.strip_partition(st.shape[0], SMALL_MESH.order, 1, 0)
     x1, it1 = strip_pcg(blocks, st, one)
     x2, it2 = out[0]
-    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
-    print(f"6x8 array, 2 strips: {it2} iterations (one rank: {it1}); rel. difference "
+    for r in range(1, world):
+        assert np.array_equal(out[0][0], out[r][0]) and out[0][1] == out[r][1]
+    print(f"6x8 array, {world} strips: {it2} iterations (one rank: {it1}); rel. difference "
           f"{np.linalg.norm(x2 - x1) / np.linalg.norm(x1):.2e}")
     assert abs(it2 - it1) <= 1
     assert np.linalg.norm(x2 - x1) <= 1e-12 * np.linalg.norm(x1)
